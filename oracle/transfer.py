@@ -1,0 +1,77 @@
+"""Structured 3:1 grid transfers (Sec. 3.2 and Sec. 6.1 of the paper).
+
+Coarsening by a rate of 3 in each coordinate direction keeps every third node (index
+multiples of 3) as a coarse node; linear interpolation fills the two fine nodes between two
+coarse nodes with weights (2/3, 1/3) and (1/3, 2/3). In several dimensions the interpolation
+is the tensor product of the 1D operators. R = P^T.
+
+Dirichlet (masked) nodes take part neither as interpolation targets nor as sources: the rows
+of masked fine nodes and the columns of masked coarse nodes are zero. This is the same as
+eliminating the Dirichlet nodes before building the hierarchy.
+
+The regional (replicated-interface) interpolation is eq. "region interp":
+[[P]] = diag(Psi_k^T P Psibar_k).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .regions import Layout, block_diag
+
+
+def coarse_count(n: int) -> int:
+    if n == 1:
+        return 1
+    if (n - 1) % 3 != 0:
+        raise ValueError(f"{n} nodes cannot be coarsened 3:1 (need 3k + 1)")
+    return (n - 1) // 3 + 1
+
+
+def linear_p_1d(n: int) -> sp.csr_matrix:
+    """n x nc linear interpolation with coarse nodes at fine indices 0, 3, 6, ..."""
+    nc = coarse_count(n)
+    if n == 1:
+        return sp.csr_matrix(np.ones((1, 1)))
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        c, rem = divmod(i, 3)
+        if rem == 0:
+            rows.append(i); cols.append(c); vals.append(1.0)
+        else:
+            w_right = rem / 3.0
+            rows += [i, i]; cols += [c, c + 1]; vals += [1.0 - w_right, w_right]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, nc))
+
+
+def composite_p(global_dims, fine_mask, coarse_mask) -> sp.csr_matrix:
+    """P on the global grid (x fastest): kron(Pz, kron(Py, Px)), masked rows/columns zero."""
+    Nx, Ny, Nz = global_dims
+    P = sp.kron(linear_p_1d(Nz), sp.kron(linear_p_1d(Ny), linear_p_1d(Nx))).tocsr()
+    keep_rows = sp.diags((~np.asarray(fine_mask, bool)).astype(float))
+    keep_cols = sp.diags((~np.asarray(coarse_mask, bool)).astype(float))
+    P = (keep_rows @ P @ keep_cols).tocsr()
+    P.eliminate_zeros()
+    return P
+
+
+def coarse_dims(global_dims):
+    return tuple(coarse_count(n) for n in global_dims)
+
+
+def coarse_slabs(slabs):
+    return tuple(tuple(coarse_count(n) for n in axis) for axis in slabs)
+
+
+def coarse_mask_from_fine(global_dims, fine_mask):
+    """Coarse nodes are co-located with fine nodes of index 3i; they inherit the mask."""
+    Nx, Ny, Nz = global_dims
+    f = np.asarray(fine_mask).reshape(Nz, Ny, Nx)
+    sz = slice(None, None, 3) if Nz > 1 else slice(None)
+    return f[sz, ::3, ::3].reshape(-1).copy()
+
+
+def regional_p(layout_f: Layout, layout_c: Layout, P: sp.csr_matrix) -> sp.csr_matrix:
+    """[[P]] = diag(Psi_k^T P Psibar_k)."""
+    return block_diag([(Pf.T @ P @ Pc).tocsr()
+                       for Pf, Pc in zip(layout_f.Psi_k, layout_c.Psi_k)])
