@@ -1,0 +1,209 @@
+/*
+ * rmg.h - C ABI of a single-GPU region multigrid library (GB300, sm_103a).
+ *
+ * Method: "Non-invasive multigrid for semi-structured grids" (arXiv 2103.11962).
+ * A composite matrix A on a mesh tiled by structured box regions is split into region
+ * matrices (Sec. 4); interface nodes are duplicated in every region that contains them
+ * (Sec. 3.1, the boolean map Psi). A regional V-cycle (Sec. 3.3 and the regional mgCycle
+ * figure of Sec. 3.6) then runs region-locally: smoothing (Sec. 3.4), 3:1 structured
+ * restriction and interpolation (Sec. 3.2, Sec. 3.3), Galerkin coarse operators computed per
+ * region (eq. "RegionalGalerkinProduct", Theorem 1), and a dense direct solve of the
+ * composite coarsest operator (Sec. 3.5). The only coupling between regions is the interface
+ * summation Psi^T Psi. The V-cycle preconditions a conjugate-gradient solve.
+ *
+ * Conventions for every entry point:
+ *  - Arrays named "device" are caller-owned CUDA device pointers on the context's device.
+ *    "host" arrays are read during the call only. const pointers are never written.
+ *  - All work is queued on the context's stream. Calls return once the work is queued,
+ *    except where a function says it synchronises.
+ *  - No C++ exception crosses the ABI. Every function returns an rmg_status. The message of
+ *    the last failure is available from rmg_last_error().
+ *  - Objects created by rmg_*_create / rmg_setup are owned by the caller and released with
+ *    the matching destroy function. The library allocates its internal buffers with
+ *    cudaMalloc on the context's device.
+ *  - Vectors are FP64. A "regional" vector has one entry per regional node; regions are
+ *    concatenated in region order and nodes inside a region are ordered x fastest. A
+ *    "composite" vector has one entry per composite node (index = global id, gid).
+ *  - A regional vector is "consistent" when all copies of an interface node hold the same
+ *    value (it is Psi^T of a composite vector).
+ */
+#ifndef RMG_H
+#define RMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmg_ctx rmg_ctx;
+typedef struct rmg_layout rmg_layout;
+typedef struct rmg_hier rmg_hier;
+
+typedef enum {
+  RMG_OK = 0,
+  RMG_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad option)      */
+  RMG_ERR_LAYOUT = 2,        /* region map does not conform (bad gids, sizes not 3k+1 ...) */
+  RMG_ERR_CUDA = 3,          /* a CUDA runtime call failed                                 */
+  RMG_ERR_NOMEM = 4,         /* device allocation failed                                   */
+  RMG_ERR_SINGULAR = 5,      /* coarsest operator not positive definite                    */
+  RMG_ERR_NOT_CONVERGED = 6, /* solver reached maxit above the tolerance                   */
+  RMG_ERR_TIMEOUT = 7,       /* a device-side wait ran out (no kernel here waits today)    */
+  RMG_ERR_STATE = 8          /* call out of order (e.g. setup before an operator is set)   */
+} rmg_status;
+
+typedef enum { RMG_SMOOTHER_JACOBI = 0, RMG_SMOOTHER_CHEBYSHEV = 1 } rmg_smoother;
+
+/* Arithmetic of the V-cycle. The outer CG always runs in FP64. */
+typedef enum {
+  RMG_PREC_FP64 = 0,            /* plain method, FP64 throughout                              */
+  RMG_PREC_FP32 = 1,            /* V-cycle vectors and coefficients in FP32                   */
+  RMG_PREC_FP32_BF16COEF = 2    /* FP32 vectors, stencil coefficients stored as BF16          */
+} rmg_precision;
+
+typedef struct {
+  int levels;            /* hierarchy levels including the finest (>= 1)                   */
+  int smoother;          /* rmg_smoother                                                   */
+  int nu1, nu2;          /* pre/post: Jacobi sweeps, or Chebyshev polynomial applications */
+  double omega;          /* Jacobi damping (Sec. 3.4)                                      */
+  int cheb_degree;       /* Chebyshev: updates of u per application (Algorithm 2)          */
+  double eig_ratio;      /* Chebyshev interval [lambda/eig_ratio, boost*lambda] (Sec. 3.4) */
+  double boost;
+  int power_iters;       /* power-method steps for lambda_max(D^-1 A)                      */
+  int power_seed_base;   /* start vector of level l: SplitMix64 stream seed_base + l        */
+  int precision;         /* rmg_precision                                                  */
+  int use_graph;         /* capture the V-cycle in a CUDA graph (1) or launch eagerly (0)  */
+} rmg_options;
+
+typedef struct {
+  int iterations;        /* products with A (0 when the initial residual already passes)  */
+  double relres;         /* final ||b - A x|| / ||b|| (recurrence residual, FP64)           */
+  double true_relres;    /* recomputed from x at the end                                   */
+  double seconds;        /* wall time of the solve (host clock, synchronised)              */
+  int vcycles;           /* preconditioner applications                                    */
+} rmg_solve_info;
+
+/* Defaults: 4 levels, Jacobi, nu1 = nu2 = 2, omega 0.67, degree 3, eig_ratio 20, boost 1.1,
+ * 10 power iterations, seed base 10, FP64, graph on. */
+void rmg_options_default(rmg_options* opts);
+
+/* Create a context on CUDA device `device` that queues work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+rmg_status rmg_create(rmg_ctx** out, int device, void* cuda_stream);
+void rmg_destroy(rmg_ctx* ctx);
+/* Message of the most recent failure on this context ("" if none). Valid until next call. */
+const char* rmg_last_error(rmg_ctx* ctx);
+/* Change the stream used by later calls (the captured V-cycle graph replays on it too). */
+rmg_status rmg_set_stream(rmg_ctx* ctx, void* cuda_stream);
+
+/*
+ * Region layout (Sec. 3.1 and Sec. 4: the application supplies, per region, the number of
+ * grid points per dimension and, per regional node, the composite node it is co-located
+ * with; the library builds Psi implicitly: multiplicities Psi Psi^T and the interface groups
+ * used for Psi^T Psi).
+ *   dim             2 or 3 (2D regions have nz = 1)
+ *   nregions        number of regions m
+ *   region_dims     host, int32[3*m]: nx, ny, nz of every region (nodes per axis)
+ *   region_gids     device, int64[n_r], n_r = sum nx*ny*nz: composite id in [0, n_composite)
+ *                   of every regional node, regions concatenated, nodes x fastest
+ *   n_composite     number of composite nodes; every one must appear in some region
+ *   dirichlet       device, uint8[n_composite] or NULL: 1 marks a masked (Dirichlet) node
+ * Errors: RMG_ERR_ARG for bad sizes, RMG_ERR_LAYOUT when a gid is out of range, a composite
+ * node is in no region, or a node is shared by more than 255 regional copies.
+ * Synchronises the stream (it reads back the interface-group count).
+ */
+rmg_status rmg_layout_create(rmg_ctx* ctx, int dim, int nregions, const int32_t* region_dims,
+                             const int64_t* region_gids, int64_t n_composite,
+                             const uint8_t* dirichlet, rmg_layout** out);
+void rmg_layout_destroy(rmg_layout* layout);
+
+/* Sizes of a layout: regional nodes, composite nodes, shared composite nodes (interface
+ * groups) and regional slots in those groups. Any pointer may be NULL. */
+rmg_status rmg_layout_sizes(rmg_layout* layout, int64_t* n_regional, int64_t* n_composite,
+                            int64_t* n_groups, int64_t* n_group_slots);
+
+/*
+ * Non-invasive operator construction (Sec. 4). The composite matrix, fully assembled, in
+ * CSR form on the device (row = composite id, entries of a row in any order). Every region
+ * k receives A_ij / q_ij for the off-diagonals it contains (q_ij = number of regions that
+ * contain both i and j) and a diagonal chosen so the region matrix reproduces A applied to
+ * the constant vector, divided by the multiplicity (row sum zero for interior rows).
+ *   stencil         5 or 9 (dim 2), 7 or 27 (dim 3): the neighbourhood every region row
+ *                   may use; an entry outside it fails with RMG_ERR_LAYOUT
+ *   rowptr, col     device int64 [n_composite + 1], [nnz]; val device double [nnz]
+ * Replaces any operator set before. Synchronises the stream (error flag read-back).
+ */
+rmg_status rmg_operator_from_csr(rmg_layout* layout, int stencil, const int64_t* rowptr,
+                                 const int64_t* col, const double* val);
+
+/* Set already-split region matrices directly: coeffs is device double[stencil * n_r],
+ * slot-major (coefficient s of regional node n at s * n_r + n). Slot order: 7-point
+ * (-z,-y,-x,0,+x,+y,+z); 5-point (-y,-x,0,+x,+y); 9/27-point: (dx+1) + 3(dy+1) [+ 9(dz+1)]. */
+rmg_status rmg_operator_from_region_stencils(rmg_layout* layout, int stencil,
+                                             const double* coeffs);
+
+/* Regional operator apply, the eq. "regional residual" with b = 0:
+ * y = Psi^T Psi [[A]] u. u and y are device regional vectors (u consistent); y is
+ * consistent on return. */
+rmg_status rmg_regional_apply(rmg_layout* layout, const double* u, double* y);
+
+/* Psi^T: regional r from composite c (device vectors). */
+rmg_status rmg_comp_to_reg(rmg_layout* layout, const double* c, double* r);
+/* Psi (average = 0: sum of copies) or (Psi Psi^T)^-1 Psi (average = 1: mean of copies). */
+rmg_status rmg_reg_to_comp(rmg_layout* layout, const double* r, double* c, int average);
+
+/*
+ * Hierarchy setup (the regional mgSetup figure of Sec. 3.6): per level the composite
+ * diagonal D~ = Psi^T Psi diag([[A]]) (Sec. 3.2), 3:1 linear interpolation per region
+ * (Sec. 3.2, coarse nodes at local multiples of 3), the regional Galerkin product
+ * [[Abar]] = [[R]] [[A]] [[P]] (eq. RegionalGalerkinProduct), Chebyshev bounds from the
+ * power method (Sec. 3.4), and on the coarsest level the composite operator
+ * Abar = Psibar [[Abar]] Psibar^T and its dense Cholesky factor (Sec. 3.5). Every region
+ * dimension must allow levels-1 coarsenings by 3 (n - 1 divisible by 3 each time) and
+ * co-located nodes must agree on being coarse points, else RMG_ERR_LAYOUT. The layout must
+ * outlive the hierarchy. Synchronises the stream.
+ */
+rmg_status rmg_setup(rmg_layout* layout, const rmg_options* opts, rmg_hier** out);
+/* Recompute all numeric setup from the layout's current operator, reusing every buffer and
+ * the captured graph (for a new operator on the same mesh). Synchronises the stream. */
+rmg_status rmg_setup_numeric(rmg_hier* hier);
+void rmg_hier_destroy(rmg_hier* hier);
+
+/* One V-cycle with zero initial guess: z = M^-1 r. r and z are device vectors, composite
+ * (layout_flag = 0) or regional and consistent (layout_flag = 1). */
+rmg_status rmg_vcycle_apply(rmg_hier* hier, const double* r, double* z, int layout_flag);
+
+/*
+ * Preconditioned conjugate gradients in FP64 with one V-cycle as preconditioner. b and x
+ * are device composite vectors (x: in = initial guess, out = solution). Entries at masked
+ * nodes of b are taken as zero. Stops when ||r||_2 / ||b||_2 <= rtol on the recurrence
+ * residual, or after maxit iterations (RMG_ERR_NOT_CONVERGED, x still written).
+ * history: host double[maxit + 1] or NULL, receives the relative residual per iteration.
+ * Synchronises the stream once per iteration (the convergence test).
+ */
+rmg_status rmg_pcg_solve(rmg_hier* hier, const double* b, double* x, double rtol, int maxit,
+                         double* history, rmg_solve_info* info);
+
+/* ---- introspection (tests and benchmarks) ------------------------------------------- */
+/* Levels, and per level: regions, regional nodes, composite id space, stencil points. */
+rmg_status rmg_hier_level_sizes(rmg_hier* hier, int level, int64_t* n_regional,
+                                int64_t* n_composite, int* stencil);
+/* Copy level data to caller device buffers (any may be NULL):
+ *   coeffs  double[stencil * n_r] region stencils (slot-major, see above), FP64 copy
+ *   dinv    double[n_r] inverse composite diagonal in regional layout
+ *   gids    int64[n_r] composite id of every regional node on that level */
+rmg_status rmg_hier_level_export(rmg_hier* hier, int level, double* coeffs, double* dinv,
+                                 int64_t* gids);
+/* Chebyshev lambda~ estimate of a level (host). */
+rmg_status rmg_hier_lambda(rmg_hier* hier, int level, double* lam);
+/* Coarsest composite matrix restricted to unmasked nodes (dense, row-major, host double
+ * [nc*nc]) and the composite ids of those unknowns (host int64[nc]). Pass NULL to query nc. */
+rmg_status rmg_hier_coarse_matrix(rmg_hier* hier, int64_t* nc, double* dense, int64_t* ids);
+/* Kernel launches queued by one V-cycle (0 when eager mode has not run yet). */
+rmg_status rmg_hier_vcycle_launches(rmg_hier* hier, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMG_H */

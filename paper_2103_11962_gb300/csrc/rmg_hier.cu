@@ -1,0 +1,713 @@
+// Hierarchy setup (regional mgSetup), the regional V-cycle (regional mgCycle) and PCG.
+#include <chrono>
+#include <cmath>
+
+#include "rmg_hier.cuh"
+#include "rmg_layout.cuh"
+#include "rmg_setup_kernels.cuh"
+
+namespace rmg {
+
+Hier::~Hier() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (graph_stream) cudaStreamDestroy(graph_stream);
+  if (pinned) cudaFreeHost(pinned);
+}
+
+namespace {
+
+template <typename T>
+__global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = a[k];
+}
+
+template <typename S, typename D>
+__global__ void k_convert(size_t n, const S* __restrict__ a, D* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    b[k] = D(a[k]);
+}
+
+__global__ void k_to_bf16(size_t n, const double* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    b[k] = __float2bfloat16_rn((float)a[k]);
+}
+
+// coarse solve: gather the averaged composite right-hand side, x = Abar^-1 rhs, replicate
+template <typename VT>
+__global__ void k_coarse_gather(int nc, const VT* __restrict__ w, const int* __restrict__ cu2slot,
+                                double* __restrict__ rc) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x)
+    rc[k] = double(w[cu2slot[k]]);
+}
+
+__global__ void k_gemv(int nc, const double* __restrict__ A, const double* __restrict__ v,
+                       double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < nc; i += nwarps) {
+    double s = 0.0;
+    const double* row = A + (size_t)i * nc;
+    for (int j = lane; j < nc; j += 32) s = fma(row[j], v[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+template <typename VT>
+__global__ void k_coarse_scatter(int n_r, const int* __restrict__ gid, const int* __restrict__ cidx,
+                                 const double* __restrict__ xc, VT* __restrict__ u) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x) {
+    const int c = cidx[gid[k]];
+    u[k] = c >= 0 ? VT(xc[c]) : VT(0);
+  }
+}
+
+// PCG scalar updates (single thread)
+__global__ void k_alpha(Scalars* sc) { sc->alpha = sc->rz / sc->pq; }
+__global__ void k_beta(Scalars* sc, int flexible) {
+  // flexible (Polak-Ribiere) form: beta = r.(z - z_old) / rz_old, with r.z_old in sc->beta
+  const double num = flexible ? sc->rz_new - sc->beta : sc->rz_new;
+  sc->beta = num / sc->rz;
+  sc->rz = sc->rz_new;
+}
+
+__global__ void __launch_bounds__(256)
+k_cg_update(int n, const double* __restrict__ p, const double* __restrict__ q,
+            const uint8_t* __restrict__ mult, const Scalars* __restrict__ sc,
+            double* __restrict__ x, double* __restrict__ r, double* __restrict__ partials) {
+  const double a = sc->alpha;
+  double s = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    x[k] = x[k] + a * p[k];
+    const double rk = r[k] - a * q[k];
+    r[k] = rk;
+    s += (rk * rk) * (1.0 / double(mult[k]));
+  }
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_p_update(int n, const double* __restrict__ z, const Scalars* __restrict__ sc,
+                           double* __restrict__ p) {
+  const double b = sc->beta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    p[k] = z[k] + b * p[k];
+}
+
+template <class Epi, typename CT, typename VT, typename AT>
+void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
+                    cudaStream_t st, int* launches) {
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+  switch (L.kind) {
+    case 5: k_stencil<5, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+    case 7: k_stencil<7, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+    case 9: k_stencil<9, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+    default: k_stencil<27, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+  }
+  RMG_LAUNCHED();
+  if (launches) ++*launches;
+  if (L.ngroups) {
+    k_groups<AT><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, st>>>(
+        L.ngroups, L.gptr.get(), L.gslot.get(), y, epi);
+    RMG_LAUNCHED();
+    if (launches) ++*launches;
+  }
+}
+
+void dot(Ctx& c, int n, const double* x, const double* y, const uint8_t* mult, double* dst,
+         int op, cudaStream_t st) {
+  const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
+  k_dot<double, double><<<g, 256, 0, st>>>(n, x, y, mult, c.partials.get());
+  RMG_LAUNCHED();
+  k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, dst, op);
+  RMG_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------- V-cycle executor
+template <typename VT, typename CT>
+struct Exec {
+  Hier& h;
+  cudaStream_t st;
+  int launches = 0;
+  std::vector<VT*> cur, oth;
+
+  Exec(Hier& hh, cudaStream_t s) : h(hh), st(s) {}
+
+  LevelVecs<VT>& V(int l);
+  const CT* coef(int l) const;
+  const VT* dinv(int l) const;
+  Scalars* sc() const { return h.sc.get(); }
+  Ctx& c() const { return *h.c; }
+  void flip(int l) { std::swap(cur[l], oth[l]); }
+
+  template <class Epi>
+  void stencil(int l, const VT* u, Epi epi) {
+    launch_stencil(c(), *h.lv[l], coef(l), u, V(l).y.get(), epi, st, &launches);
+  }
+
+  int elementwise_grid(int n) const { return persistent_grid(c(), (n + 255) / 256); }
+
+  void cheb_step(int l, int k) {   // k >= 1
+    const Level& L = *h.lv[l];
+    (void)L;
+    EpiCheb<VT> e{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c1[l][k], &sc()->cheb_c2[l][k],
+                  V(l).d.get(), oth[l]};
+    stencil(l, cur[l], e);
+    flip(l);
+  }
+
+  void smooth(int l, int nu, bool from_zero) {
+    const Level& L = *h.lv[l];
+    const int n = L.n_r;
+    const VT omega = VT(h.o.omega);
+    if (h.o.smoother == RMG_SMOOTHER_JACOBI) {
+      for (int s = 0; s < nu; ++s) {
+        if (s == 0 && from_zero) {
+          k_jacobi_zero<VT><<<elementwise_grid(n), 256, 0, st>>>(n, V(l).b.get(), dinv(l), omega,
+                                                                 oth[l]);
+          RMG_LAUNCHED();
+          ++launches;
+        } else {
+          stencil(l, cur[l], EpiJacobi<VT>{cur[l], V(l).b.get(), dinv(l), omega, oth[l]});
+        }
+        flip(l);
+      }
+    } else {
+      for (int a = 0; a < nu; ++a) {
+        if (a == 0 && from_zero) {
+          k_cheb0_zero<VT><<<elementwise_grid(n), 256, 0, st>>>(n, V(l).b.get(), dinv(l),
+                                                                &sc()->cheb_c2[l][0],
+                                                                V(l).d.get(), oth[l]);
+          RMG_LAUNCHED();
+          ++launches;
+        } else {
+          stencil(l, cur[l], EpiCheb0<VT>{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c2[l][0],
+                                          V(l).d.get(), oth[l]});
+        }
+        flip(l);
+        for (int k = 1; k < h.o.cheb_degree; ++k) cheb_step(l, k);
+      }
+    }
+  }
+
+  void residual(int l) { stencil(l, cur[l], EpiResid<VT>{V(l).b.get(), V(l).r.get()}); }
+
+  void restrict_to(int l) {
+    const Level& F = *h.lv[l];
+    const Level& C = *h.lv[l + 1];
+    const Grid Gc = C.grid();
+    const int gb = persistent_grid(c(), Gc.ntiles);
+    if (F.dim == 3)
+      k_restrict<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), F.mult.get(),
+                                              C.mask.get(), C.mult.get(), V(l + 1).b.get(),
+                                              V(l + 1).y.get());
+    else
+      k_restrict<2, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), F.mult.get(),
+                                              C.mask.get(), C.mult.get(), V(l + 1).b.get(),
+                                              V(l + 1).y.get());
+    RMG_LAUNCHED();
+    ++launches;
+    if (C.ngroups) {
+      k_groups<VT><<<persistent_grid(c(), (C.ngroups + 255) / 256), 256, 0, st>>>(
+          C.ngroups, C.gptr.get(), C.gslot.get(), V(l + 1).y.get(), EpiStore<VT>{V(l + 1).b.get()});
+      RMG_LAUNCHED();
+      ++launches;
+    }
+  }
+
+  void prolong(int l) {
+    const Level& F = *h.lv[l];
+    const Level& C = *h.lv[l + 1];
+    const Grid Gf = F.grid();
+    const int gb = persistent_grid(c(), Gf.ntiles);
+    if (F.dim == 3)
+      k_prolong<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), F.mask.get(), cur[l + 1], cur[l]);
+    else
+      k_prolong<2, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), F.mask.get(), cur[l + 1], cur[l]);
+    RMG_LAUNCHED();
+    ++launches;
+  }
+
+  void coarse(int l) {
+    const Level& L = *h.lv[l];
+    const int nc = h.nc;
+    if (nc > 0) {
+      k_coarse_gather<VT><<<elementwise_grid(nc), 256, 0, st>>>(nc, V(l).b.get(), h.cu2slot.get(),
+                                                                h.rc.get());
+      RMG_LAUNCHED();
+      const int warps_needed = nc;
+      const int blocks = std::max(1, std::min(c().nsm * 4, (warps_needed * 32 + 255) / 256));
+      k_gemv<<<blocks, 256, 0, st>>>(nc, h.Ainv.get(), h.rc.get(), h.xc.get());
+      RMG_LAUNCHED();
+      launches += 2;
+    }
+    k_coarse_scatter<VT><<<elementwise_grid(L.n_r), 256, 0, st>>>(L.n_r, L.gid.get(), h.cidx.get(),
+                                                                  h.xc.get(), cur[l]);
+    RMG_LAUNCHED();
+    ++launches;
+  }
+
+  int level0_flips() const {
+    const int per = (h.o.smoother == RMG_SMOOTHER_JACOBI) ? 1 : h.o.cheb_degree;
+    return (h.o.nu1 + h.o.nu2) * per;
+  }
+
+  void run() {
+    const int Lv = h.levels();
+    cur.assign(Lv, nullptr);
+    oth.assign(Lv, nullptr);
+    for (int l = 0; l < Lv; ++l) { cur[l] = V(l).u.get(); oth[l] = V(l).u2.get(); }
+    if (Lv > 1 && (level0_flips() & 1)) std::swap(cur[0], oth[0]);
+    for (int l = 0; l < Lv - 1; ++l) {
+      smooth(l, h.o.nu1, true);
+      residual(l);
+      restrict_to(l);
+    }
+    coarse(Lv - 1);
+    for (int l = Lv - 2; l >= 0; --l) {
+      prolong(l);
+      smooth(l, h.o.nu2, false);
+    }
+  }
+};
+
+template <> LevelVecs<double>& Exec<double, double>::V(int l) { return h.v64[l]; }
+template <> const double* Exec<double, double>::coef(int l) const { return h.lv[l]->coef.get(); }
+template <> const double* Exec<double, double>::dinv(int l) const { return h.lv[l]->dinv.get(); }
+template <> LevelVecs<float>& Exec<float, float>::V(int l) { return h.v32[l]; }
+template <> const float* Exec<float, float>::coef(int l) const { return h.lv[l]->coef32.get(); }
+template <> const float* Exec<float, float>::dinv(int l) const { return h.lv[l]->dinv32.get(); }
+template <> LevelVecs<float>& Exec<float, __nv_bfloat16>::V(int l) { return h.v32[l]; }
+template <> const __nv_bfloat16* Exec<float, __nv_bfloat16>::coef(int l) const {
+  return h.lv[l]->coef16.get();
+}
+template <> const float* Exec<float, __nv_bfloat16>::dinv(int l) const {
+  return h.lv[l]->dinv32.get();
+}
+
+int run_cycle(Hier& h, cudaStream_t st) {
+  if (h.o.precision == RMG_PREC_FP64) {
+    Exec<double, double> e(h, st);
+    e.run();
+    return e.launches;
+  } else if (h.o.precision == RMG_PREC_FP32) {
+    Exec<float, float> e(h, st);
+    e.run();
+    return e.launches;
+  } else {
+    Exec<float, __nv_bfloat16> e(h, st);
+    e.run();
+    return e.launches;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------- setup
+static void coarsen_level(Hier& h, const Level& F, Level& C) {
+  Ctx& c = *h.c;
+  std::vector<int> cd(3 * F.nreg);
+  for (int r = 0; r < F.nreg; ++r)
+    for (int a = 0; a < 3; ++a) {
+      const int n = F.hdims[3 * r + a];
+      if (n == 1 && (F.dim == 2 && a == 2)) { cd[3 * r + a] = 1; continue; }
+      RMG_REQUIRE(n >= 4 && (n - 1) % 3 == 0, RMG_ERR_LAYOUT,
+                  "region " + std::to_string(r) + " has " + std::to_string(n) +
+                      " nodes along an axis; 3:1 coarsening needs 3k+1 with k >= 1");
+      cd[3 * r + a] = (n - 1) / 3 + 1;
+    }
+  set_geometry(C, F.dim, F.nreg, cd.data());
+  DBuf<int> flag(F.ncomp), sel(F.ncomp), cid(F.ncomp);
+  RMG_CUDA(cudaMemsetAsync(flag.get(), 0, flag.bytes(), c.stream));
+  const Grid Gf = F.grid();
+  k_coarse_flags<<<persistent_grid(c, Gf.ntiles), kTile, 0, c.stream>>>(Gf, F.dim, F.gid.get(),
+                                                                         flag.get());
+  RMG_LAUNCHED();
+  k_coarse_select<<<persistent_grid(c, (F.ncomp + 255) / 256), 256, 0, c.stream>>>(
+      F.ncomp, flag.get(), sel.get(), c.d_err.get());
+  RMG_LAUNCHED();
+  C.ncomp = exclusive_scan(c, sel.get(), cid.get(), F.ncomp);
+  c.check_device_error("rmg_setup");
+  C.gid.alloc(C.n_r);
+  DBuf<uint8_t> cmask(C.n_r);
+  DBuf<int> count(C.ncomp);
+  RMG_CUDA(cudaMemsetAsync(count.get(), 0, count.bytes(), c.stream));
+  const Grid Gc = C.grid();
+  k_coarse_gids<<<persistent_grid(c, Gc.ntiles), kTile, 0, c.stream>>>(
+      Gc, F.dim, F.regions.get(), F.gid.get(), F.mask.get(), cid.get(), C.gid.get(), cmask.get(),
+      count.get());
+  RMG_LAUNCHED();
+  build_groups(c, C, nullptr, cmask.get(), count);
+  c.check_device_error("rmg_setup");
+  C.kind = coarse_kind(F.kind);
+  C.coef.alloc((size_t)C.kind * C.n_r);
+}
+
+void hier_build(Hier& h) {
+  Ctx& c = *h.c;
+  RMG_REQUIRE(h.layout->has_operator, RMG_ERR_STATE, "rmg_setup needs an operator on the layout");
+  const rmg_options& o = h.o;
+  RMG_REQUIRE(o.levels >= 1 && o.levels <= 16, RMG_ERR_ARG, "levels must be in [1, 16]");
+  RMG_REQUIRE(o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 0, RMG_ERR_ARG, "bad nu1/nu2");
+  RMG_REQUIRE(o.smoother == RMG_SMOOTHER_JACOBI || o.smoother == RMG_SMOOTHER_CHEBYSHEV,
+              RMG_ERR_ARG, "unknown smoother");
+  RMG_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, RMG_ERR_ARG, "cheb_degree in [1, 8]");
+  RMG_REQUIRE(o.precision >= 0 && o.precision <= 2, RMG_ERR_ARG, "unknown precision");
+  RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1, RMG_ERR_ARG,
+              "bad Chebyshev options");
+  h.lv.push_back(&h.layout->L0);
+  for (int l = 1; l < o.levels; ++l) {
+    h.own.emplace_back(new Level());
+    coarsen_level(h, *h.lv.back(), *h.own.back());
+    h.lv.push_back(h.own.back().get());
+  }
+  const int Lv = h.levels();
+  h.v64.resize(Lv);
+  for (int l = 0; l < Lv; ++l) {
+    h.lv[l]->dinv.alloc(h.lv[l]->n_r);
+    h.v64[l].alloc(h.lv[l]->n_r);
+  }
+  if (h.mixed()) {
+    h.v32.resize(Lv);
+    for (int l = 0; l < Lv; ++l) {
+      Level& L = *h.lv[l];
+      h.v32[l].alloc(L.n_r);
+      L.dinv32.alloc(L.n_r);
+      if (o.precision == RMG_PREC_FP32) L.coef32.alloc((size_t)L.kind * L.n_r);
+      else L.coef16.alloc((size_t)L.kind * L.n_r);
+    }
+  }
+  h.sc.alloc(1);
+  RMG_CUDA(cudaMemsetAsync(h.sc.get(), 0, sizeof(Scalars), c.stream));
+  const int n0 = h.lv[0]->n_r;
+  h.x.alloc(n0); h.p.alloc(n0); h.q.alloc(n0); h.tmp.alloc(n0);
+  h.r.alloc(n0); h.z.alloc(n0); h.zold.alloc(n0);
+  RMG_CUDA(cudaHostAlloc(&h.pinned, 64 * sizeof(double), cudaHostAllocDefault));
+  // coarsest composite maps
+  Level& Lc = *h.lv[Lv - 1];
+  DBuf<int> freeflag(Lc.ncomp), pos(Lc.ncomp);
+  k_coarse_free<<<persistent_grid(c, (Lc.ncomp + 255) / 256), 256, 0, c.stream>>>(
+      Lc.ncomp, Lc.c2r.get(), Lc.mask.get(), freeflag.get());
+  RMG_LAUNCHED();
+  h.nc = exclusive_scan(c, freeflag.get(), pos.get(), Lc.ncomp);
+  RMG_REQUIRE((long long)h.nc * h.nc < (1LL << 31), RMG_ERR_ARG,
+              "coarsest level too large for the dense solver (add levels)");
+  h.cidx.alloc(Lc.ncomp);
+  h.cu2slot.alloc(std::max(1, h.nc));
+  h.cu2gid.alloc(std::max(1, h.nc));
+  k_coarse_maps<<<persistent_grid(c, (Lc.ncomp + 255) / 256), 256, 0, c.stream>>>(
+      Lc.ncomp, freeflag.get(), pos.get(), Lc.c2r.get(), h.cidx.get(), h.cu2slot.get(),
+      h.cu2gid.get());
+  RMG_LAUNCHED();
+  const size_t nc2 = (size_t)std::max(1, h.nc) * std::max(1, h.nc);
+  h.Mfac.alloc(nc2); h.X.alloc(nc2); h.Ainv.alloc(nc2);
+  h.xc.alloc(std::max(1, h.nc)); h.rc.alloc(std::max(1, h.nc));
+  RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
+  RMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+static void compute_dinv(Hier& h, Level& L) {
+  Ctx& c = *h.c;
+  const int gb = persistent_grid(c, (L.n_r + 255) / 256);
+  double* y = h.v64[&L == h.lv[0] ? 0 : 0].y.get();
+  // use this level's own scratch
+  for (int l = 0; l < h.levels(); ++l) if (h.lv[l] == &L) y = h.v64[l].y.get();
+  switch (L.kind) {
+    case 5: k_diag_local<5><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
+    case 7: k_diag_local<7><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
+    case 9: k_diag_local<9><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
+    default: k_diag_local<27><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
+  }
+  RMG_LAUNCHED();
+  if (L.ngroups) {
+    k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
+        L.ngroups, L.gptr.get(), L.gslot.get(), y, EpiRecip{L.dinv.get()});
+    RMG_LAUNCHED();
+  }
+}
+
+static void galerkin(Hier& h, const Level& F, Level& C) {
+  Ctx& c = *h.c;
+  const int gb = persistent_grid(c, (C.n_r + kRapBS - 1) / kRapBS, 16);
+#define RMG_RAP(FK, CK, D)                                                                  \
+  k_rap<FK, CK, D><<<gb, kRapBS, 0, c.stream>>>(C.n_r, C.regions.get(), C.nreg, F.regions.get(), \
+                                                F.coef.get(), F.n_r, F.mask.get(), C.mask.get(),  \
+                                                C.mult.get(), C.coef.get())
+  switch (F.kind) {
+    case 5: RMG_RAP(5, 9, 2); break;
+    case 9: RMG_RAP(9, 9, 2); break;
+    case 7: RMG_RAP(7, 27, 3); break;
+    default: RMG_RAP(27, 27, 3); break;
+  }
+#undef RMG_RAP
+  RMG_LAUNCHED();
+}
+
+static void power_method(Hier& h, int l) {
+  Ctx& c = *h.c;
+  Level& L = *h.lv[l];
+  cudaStream_t st = c.stream;
+  LevelVecs<double>& V = h.v64[l];
+  const int n = L.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  Scalars* sc = h.sc.get();
+  k_power_init<<<eg, 256, 0, st>>>(n, L.gid.get(), L.mask.get(),
+                                   (unsigned long long)(h.o.power_seed_base + l), V.u.get());
+  RMG_LAUNCHED();
+  dot(c, n, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
+  k_scale_div<<<eg, 256, 0, st>>>(n, V.u.get(), &sc->pw_norm, V.u.get());
+  RMG_LAUNCHED();
+  for (int it = 0; it < h.o.power_iters; ++it) {
+    launch_stencil(c, L, L.coef.get(), V.u.get(), V.y.get(),
+                   EpiScaled<double>{L.dinv.get(), V.r.get()}, st, nullptr);
+    dot(c, n, V.r.get(), V.r.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
+    k_scale_div<<<eg, 256, 0, st>>>(n, V.r.get(), &sc->pw_norm, V.u.get());
+    RMG_LAUNCHED();
+  }
+  launch_stencil(c, L, L.coef.get(), V.u.get(), V.y.get(),
+                 EpiScaled<double>{L.dinv.get(), V.r.get()}, st, nullptr);
+  dot(c, n, V.u.get(), V.r.get(), L.mult.get(), &sc->pw_num, FIN_STORE, st);
+  dot(c, n, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_den, FIN_STORE, st);
+  k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
+  RMG_LAUNCHED();
+}
+
+static void coarse_factor(Hier& h) {
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  Level& L = *h.lv[h.levels() - 1];
+  const int nc = h.nc;
+  if (nc == 0) return;
+  RMG_CUDA(cudaMemsetAsync(h.Mfac.get(), 0, (size_t)nc * nc * sizeof(double), st));
+  const int gb = persistent_grid(c, (L.ncomp + 127) / 128);
+#define RMG_ASM(K)                                                                              \
+  k_coarse_assemble<K><<<gb, 128, 0, st>>>(L.ncomp, nc, L.regions.get(), L.nreg, L.n_r,         \
+                                           L.coef.get(), L.gid.get(), h.cidx.get(), L.c2r.get(), \
+                                           L.cgrp.get(), L.gptr.get(), L.gslot.get(), h.Mfac.get())
+  switch (L.kind) {
+    case 5: RMG_ASM(5); break;
+    case 7: RMG_ASM(7); break;
+    case 9: RMG_ASM(9); break;
+    default: RMG_ASM(27); break;
+  }
+#undef RMG_ASM
+  RMG_LAUNCHED();
+  // keep the assembled matrix for introspection in X before factorising
+  RMG_CUDA(cudaMemcpyAsync(h.X.get(), h.Mfac.get(), (size_t)nc * nc * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
+  for (int k0 = 0; k0 < nc; k0 += kNB) {
+    k_chol_diag<<<1, 256, 0, st>>>(h.Mfac.get(), nc, k0, c.d_err.get());
+    RMG_LAUNCHED();
+    const int k1 = std::min(nc, k0 + kNB);
+    if (k1 < nc) {
+      const int rows = nc - k1;
+      k_chol_panel<<<std::max(1, (rows + 127) / 128), 128, 0, st>>>(h.Mfac.get(), nc, k0);
+      RMG_LAUNCHED();
+      const int tiles = (rows + 15) / 16;
+      k_chol_update<<<dim3(tiles, tiles), dim3(16, 16), 0, st>>>(h.Mfac.get(), nc, k0, k1);
+      RMG_LAUNCHED();
+    }
+  }
+  c.check_device_error("rmg_setup (coarse factorisation)");
+  // the assembled matrix is kept in Ainv's slot until the inverse overwrites it
+  DBuf<double> Linv((size_t)nc * nc);
+  k_trinv<<<std::max(1, (nc + 63) / 64), 64, 0, st>>>(h.Mfac.get(), nc, Linv.get());
+  RMG_LAUNCHED();
+  const int t = (nc + 15) / 16;
+  k_xtx<<<dim3(t, t), dim3(16, 16), 0, st>>>(Linv.get(), nc, h.Ainv.get());
+  RMG_LAUNCHED();
+  RMG_CUDA(cudaStreamSynchronize(st));
+}
+
+static void make_low_precision(Hier& h) {
+  Ctx& c = *h.c;
+  for (int l = 0; l < h.levels(); ++l) {
+    Level& L = *h.lv[l];
+    const size_t nco = (size_t)L.kind * L.n_r;
+    const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
+    if (h.o.precision == RMG_PREC_FP32)
+      k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
+    else
+      k_to_bf16<<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef16.get());
+    RMG_LAUNCHED();
+    k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.n_r, L.dinv.get(), L.dinv32.get());
+    RMG_LAUNCHED();
+  }
+}
+
+void hier_numeric(Hier& h) {
+  Ctx& c = *h.c;
+  const int Lv = h.levels();
+  compute_dinv(h, *h.lv[0]);
+  for (int l = 0; l + 1 < Lv; ++l) {
+    galerkin(h, *h.lv[l], *h.lv[l + 1]);
+    compute_dinv(h, *h.lv[l + 1]);
+  }
+  if (h.o.smoother == RMG_SMOOTHER_CHEBYSHEV)
+    for (int l = 0; l + 1 < Lv; ++l) power_method(h, l);
+  coarse_factor(h);
+  if (h.mixed()) make_low_precision(h);
+  RMG_CUDA(cudaMemcpyAsync(&h.hsc, h.sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
+  RMG_CUDA(cudaStreamSynchronize(c.stream));
+  if (h.o.use_graph && !h.gexec) {
+    RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
+    RMG_CUDA(cudaStreamBeginCapture(h.graph_stream, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    try {
+      launches = run_cycle(h, h.graph_stream);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h.graph_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    RMG_CUDA(cudaStreamEndCapture(h.graph_stream, &h.graph));
+    RMG_CUDA(cudaGraphInstantiate(&h.gexec, h.graph, 0));
+    h.launches = launches;
+  }
+}
+
+void vcycle(Hier& h) {
+  if (h.gexec) {
+    RMG_CUDA(cudaGraphLaunch(h.gexec, h.c->stream));
+  } else {
+    h.launches = run_cycle(h, h.c->stream);
+  }
+}
+
+// r, z: FP64 regional or composite device vectors.
+void vcycle_apply(Hier& h, const double* r, double* z, int regional) {
+  Ctx& c = *h.c;
+  const Level& L0 = *h.lv[0];
+  const int n = L0.n_r, g = persistent_grid(c, (n + 255) / 256);
+  double* b64 = h.v64[0].b.get();
+  if (regional) k_copy<double><<<g, 256, 0, c.stream>>>(n, r, b64);
+  else comp_to_reg(c, L0, r, b64, true);
+  RMG_LAUNCHED();
+  if (h.mixed()) {
+    k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)n, b64, h.v32[0].b.get());
+    RMG_LAUNCHED();
+  }
+  vcycle(h);
+  double* u64 = h.v64[0].u.get();
+  if (h.mixed()) {
+    k_convert<float, double><<<g, 256, 0, c.stream>>>((size_t)n, h.v32[0].u.get(), u64);
+    RMG_LAUNCHED();
+  }
+  if (regional) k_copy<double><<<g, 256, 0, c.stream>>>(n, u64, z);
+  else reg_to_comp(c, L0, u64, z, 1);
+  RMG_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------- PCG
+void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, double* history,
+               rmg_solve_info* info) {
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  const Level& L0 = *h.lv[0];
+  const int n = L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  const int dg = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
+  Scalars* sc = h.sc.get();
+  const bool mixed = h.mixed();
+  double* rvec = h.v64[0].b.get();     // the V-cycle reads its right-hand side here
+  double* zvec = h.v64[0].u.get();     // and leaves its result here (FP64 cycle)
+  double* breg = h.tmp.get();
+  const auto t0 = std::chrono::steady_clock::now();
+  comp_to_reg(c, L0, b, breg, true);
+  comp_to_reg(c, L0, xout, h.x.get(), true);
+  // r = b - A x
+  launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
+                 EpiResid<double>{breg, rvec}, st, nullptr);
+  dot(c, n, breg, breg, L0.mult.get(), &sc->bb, FIN_STORE, st);
+  dot(c, n, rvec, rvec, L0.mult.get(), &sc->rr, FIN_STORE, st);
+  auto read2 = [&](double* a, double* bb) {
+    RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RMG_CUDA(cudaMemcpyAsync(h.pinned + 1, &sc->bb, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RMG_CUDA(cudaStreamSynchronize(st));
+    *a = h.pinned[0];
+    *bb = h.pinned[1];
+  };
+  double rr = 0, bb = 0;
+  read2(&rr, &bb);
+  const double bnorm = std::sqrt(bb);
+  double relres = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
+  if (history) history[0] = relres;
+  int it = 0, ncyc = 0;
+  auto precondition = [&]() {
+    if (mixed) {
+      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, rvec, h.v32[0].b.get());
+      RMG_LAUNCHED();
+      vcycle(h);
+      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, h.v32[0].u.get(), zvec);
+      RMG_LAUNCHED();
+    } else {
+      vcycle(h);
+    }
+    ++ncyc;
+  };
+  int status_conv = 0;
+  if (relres > rtol && bnorm > 0) {
+    precondition();
+    dot(c, n, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
+    k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.p.get());
+    RMG_LAUNCHED();
+    if (mixed) {
+      k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+      RMG_LAUNCHED();
+    }
+    for (it = 1; it <= maxit; ++it) {
+      launch_stencil(c, L0, L0.coef.get(), h.p.get(), h.v64[0].y.get(),
+                     EpiStore<double>{h.q.get()}, st, nullptr);
+      dot(c, n, h.p.get(), h.q.get(), L0.mult.get(), &sc->pq, FIN_STORE, st);
+      k_alpha<<<1, 1, 0, st>>>(sc);
+      RMG_LAUNCHED();
+      k_cg_update<<<dg, 256, 0, st>>>(n, h.p.get(), h.q.get(), L0.mult.get(), sc, h.x.get(), rvec,
+                                     c.partials.get());
+      RMG_LAUNCHED();
+      k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rr, FIN_STORE);
+      RMG_LAUNCHED();
+      read2(&rr, &bb);
+      relres = std::sqrt(rr) / bnorm;
+      if (history) history[it] = relres;
+      if (relres <= rtol) { status_conv = 1; break; }
+      precondition();
+      dot(c, n, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
+      if (mixed) {
+        dot(c, n, rvec, h.zold.get(), L0.mult.get(), &sc->beta, FIN_STORE, st);
+        k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+        RMG_LAUNCHED();
+      }
+      k_beta<<<1, 1, 0, st>>>(sc, mixed ? 1 : 0);
+      RMG_LAUNCHED();
+      k_p_update<<<eg, 256, 0, st>>>(n, zvec, sc, h.p.get());
+      RMG_LAUNCHED();
+    }
+    if (it > maxit) it = maxit;
+  } else {
+    status_conv = 1;
+  }
+  reg_to_comp(c, L0, h.x.get(), xout, 1);
+  // true residual from the final iterate
+  launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
+                 EpiResid<double>{breg, h.q.get()}, st, nullptr);
+  dot(c, n, h.q.get(), h.q.get(), L0.mult.get(), &sc->rr, FIN_STORE, st);
+  double rtrue = 0;
+  read2(&rtrue, &bb);
+  const auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iterations = it;
+    info->relres = relres;
+    info->true_relres = bnorm > 0 ? std::sqrt(rtrue) / bnorm : 0.0;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    info->vcycles = ncyc;
+  }
+  if (!status_conv)
+    throw Error(RMG_ERR_NOT_CONVERGED, "PCG reached maxit with relres " + std::to_string(relres));
+}
+
+}  // namespace rmg

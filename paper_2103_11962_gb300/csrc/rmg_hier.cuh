@@ -1,0 +1,59 @@
+// The regional multigrid hierarchy and its solve phase.
+#pragma once
+
+#include <memory>
+
+#include "rmg_internal.cuh"
+
+namespace rmg {
+
+// Work vectors of one level in the cycle's arithmetic type VT.
+template <typename VT>
+struct LevelVecs {
+  DBuf<VT> u, u2, b, r, y, d;
+  void alloc(int n) {
+    u.alloc(n); u2.alloc(n); b.alloc(n); r.alloc(n); y.alloc(n); d.alloc(n);
+  }
+};
+
+struct Hier {
+  rmg_layout* layout = nullptr;
+  Ctx* c = nullptr;
+  rmg_options o{};
+  std::vector<std::unique_ptr<Level>> own;   // levels 1..L-1
+  std::vector<Level*> lv;                    // all levels; lv[0] is the layout's level
+  std::vector<LevelVecs<double>> v64;
+  std::vector<LevelVecs<float>> v32;
+  DBuf<Scalars> sc;
+  Scalars hsc{};                             // host copy after setup
+  // coarsest composite level
+  int nc = 0;
+  DBuf<int> cidx, cu2slot;
+  DBuf<long long> cu2gid;
+  DBuf<double> Mfac, X, Ainv, xc, rc;
+  // graph of one V-cycle
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int launches = 0;
+  // PCG work vectors (regional, FP64)
+  DBuf<double> x, r, z, p, q, zold, tmp;
+  double* pinned = nullptr;                  // host-mapped residual read-back
+
+  ~Hier();
+  int levels() const { return (int)lv.size(); }
+  bool mixed() const { return o.precision != RMG_PREC_FP64; }
+};
+
+void hier_build(Hier& h);          // symbolic: coarse layouts, buffers
+void hier_numeric(Hier& h);        // numeric: diagonals, RAP, lambda, coarse factor, graph
+void vcycle(Hier& h);              // lv[0] rhs in v64[0].b (or v32[0].b) -> result in .u
+void vcycle_apply(Hier& h, const double* r, double* z, int regional);
+void pcg_solve(Hier& h, const double* b, double* x, double rtol, int maxit, double* history,
+               rmg_solve_info* info);
+
+}  // namespace rmg
+
+struct rmg_hier {
+  rmg::Hier h;
+};

@@ -1,0 +1,308 @@
+// Device kernels of the regional V-cycle and its setup.
+//
+// Every node-parallel kernel is a persistent grid-stride loop over a tile list that covers
+// all regions of a level (one launch batches all regions, whatever their sizes). A tile is a
+// run of up to kTile consecutive nodes of one region; blockDim.x == kTile.
+//
+// The interface summation Psi^T Psi (Sec. 3.1) is split in two phases. Phase A applies the
+// region stencil at every node; a node with a single copy finishes its update at once, a
+// node shared by several regions stores its partial row result y[n]. Phase B runs over the
+// interface groups (the copies of one shared composite node), sums the partial results in
+// ascending slot order and applies the same epilogue to every copy, so the copies stay
+// identical ("consistent").
+#pragma once
+
+#include "rmg_internal.cuh"
+
+namespace rmg {
+
+__device__ __forceinline__ void decode(int li, const RegionDev& R, int& i, int& j, int& l) {
+  i = li % R.nx;
+  const int rest = li / R.nx;
+  j = rest % R.ny;
+  l = rest / R.ny;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// Region containing regional node n (binary search over region offsets).
+__device__ __forceinline__ int region_of(const RegionDev* R, int nreg, int n) {
+  int lo = 0, hi = nreg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (R[mid].off <= n) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+#define RMG_FOR_NODES(G)                                                       \
+  for (int t_ = blockIdx.x; t_ < (G).ntiles; t_ += gridDim.x) {                \
+    const Tile tile_ = (G).tiles[t_];                                          \
+    const RegionDev R = (G).regions[tile_.region];                             \
+    const int li = tile_.start + (int)threadIdx.x;                             \
+    if (li >= R.nx * R.ny * R.nz) continue;                                    \
+    const int n = R.off + li;
+
+#define RMG_END_FOR_NODES }
+
+// ------------------------------------------------------------------ stencil application
+// au = sum_s coef[s][n] * u[n + off(s)] over the neighbours inside the region.
+template <int KIND, typename CT, typename VT, typename AT>
+__device__ __forceinline__ AT stencil_row(const CT* __restrict__ coef, const VT* __restrict__ u,
+                                          int n, int n_r, int i, int j, int l,
+                                          const RegionDev& R) {
+  using S = Sten<KIND>;
+  AT au = AT(0);
+  const int sx = 1, sy = R.nx, sz = R.nx * R.ny;
+#pragma unroll
+  for (int s = 0; s < S::S; ++s) {
+    const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+    bool ok = true;
+    if (dx < 0) ok &= (i > 0);
+    if (dx > 0) ok &= (i < R.nx - 1);
+    if (dy < 0) ok &= (j > 0);
+    if (dy > 0) ok &= (j < R.ny - 1);
+    if (dz < 0) ok &= (l > 0);
+    if (dz > 0) ok &= (l < R.nz - 1);
+    if (ok) {
+      const AT c = AT(coef[(size_t)s * (size_t)n_r + n]);
+      const AT v = AT(u[n + dx * sx + dy * sy + dz * sz]);
+      au = fma(c, v, au);
+    }
+  }
+  return au;
+}
+
+template <typename T> __device__ __forceinline__ T to_acc(T v) { return v; }
+
+// Phase A: stencil at every node; single-copy nodes finish through the epilogue.
+template <int KIND, typename CT, typename VT, typename AT, class Epi>
+__global__ void __launch_bounds__(kTile)
+k_stencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
+          const uint8_t* __restrict__ mult, AT* __restrict__ y, Epi epi) {
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    decode(li, R, i, j, l);
+    const AT au = stencil_row<KIND, CT, VT, AT>(coef, u, n, G.n_r, i, j, l, R);
+    if (mult[n] > 1) y[n] = au; else epi(n, au);
+  RMG_END_FOR_NODES
+}
+
+// Phase B: interface groups. y holds the partial row results of every copy.
+template <typename AT, class Epi>
+__global__ void __launch_bounds__(256)
+k_groups(int ngroups, const int* __restrict__ gptr, const int* __restrict__ gslot,
+         const AT* __restrict__ y, Epi epi) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+    const int a = gptr[g], e = gptr[g + 1];
+    AT s = AT(0);
+    for (int k = a; k < e; ++k) s += y[gslot[k]];
+    for (int k = a; k < e; ++k) epi(gslot[k], s);
+  }
+}
+
+// ------------------------------------------------------------------ epilogues
+template <typename T>
+struct EpiStore {                 // out = A u
+  T* out;
+  __device__ void operator()(int n, T au) const { out[n] = au; }
+};
+
+template <typename T>
+struct EpiScaled {                // out = D~^-1 A u (power method)
+  const T* dinv; T* out;
+  __device__ void operator()(int n, T au) const { out[n] = dinv[n] * au; }
+};
+
+template <typename T>
+struct EpiResid {                 // r = b - A u
+  const T* b; T* r;
+  __device__ void operator()(int n, T au) const { r[n] = b[n] - au; }
+};
+
+template <typename T>
+struct EpiJacobi {                // u_out = u + omega D~^-1 (b - A u)
+  const T* u; const T* b; const T* dinv; T omega; T* uo;
+  __device__ void operator()(int n, T au) const {
+    const T r = b[n] - au;
+    uo[n] = fma(omega * dinv[n], r, u[n]);
+  }
+};
+
+template <typename T>
+struct EpiCheb0 {                 // first Chebyshev step: d = D~^-1 r / theta, u_out = u + d
+  const T* u; const T* b; const T* dinv; const double* c2; T* d; T* uo;
+  __device__ void operator()(int n, T au) const {
+    const T r = b[n] - au;
+    const T dn = (dinv[n] * r) * T(*c2);
+    d[n] = dn;
+    uo[n] = u[n] + dn;
+  }
+};
+
+template <typename T>
+struct EpiCheb {                  // d = c1 d + c2 D~^-1 r, u_out = u + d
+  const T* u; const T* b; const T* dinv; const double* c1; const double* c2; T* d; T* uo;
+  __device__ void operator()(int n, T au) const {
+    const T r = b[n] - au;
+    const T dn = T(*c1) * d[n] + (T(*c2) * dinv[n]) * r;
+    d[n] = dn;
+    uo[n] = u[n] + dn;
+  }
+};
+
+// ------------------------------------------------------------------ elementwise
+template <typename T>
+__global__ void k_jacobi_zero(int n, const T* __restrict__ b, const T* __restrict__ dinv,
+                              T omega, T* __restrict__ uo) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    uo[k] = (omega * dinv[k]) * b[k];
+}
+
+template <typename T>
+__global__ void k_cheb0_zero(int n, const T* __restrict__ b, const T* __restrict__ dinv,
+                             const double* __restrict__ c2, T* __restrict__ d,
+                             T* __restrict__ uo) {
+  const T c = T(*c2);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const T dn = (dinv[k] * b[k]) * c;
+    d[k] = dn;
+    uo[k] = dn;
+  }
+}
+
+// ------------------------------------------------------------------ transfers (Sec. 3.3)
+// 1D linear 3:1 weight of the coarse node at fine offset a in [-2, 2] from it. The right
+// weight of a fine node with remainder rem is rem/3 and the left one 1 - rem/3.
+__device__ __forceinline__ double w1d(int a) {
+  switch (a) {
+    case -2: return 1.0 / 3.0;          // rem 1, coarse node on the right
+    case -1: return 2.0 / 3.0;          // rem 2, coarse node on the right
+    case 0: return 1.0;
+    case 1: return 1.0 - 1.0 / 3.0;     // rem 1, coarse node on the left
+    default: return 1.0 - 2.0 / 3.0;    // rem 2, coarse node on the left
+  }
+}
+
+// Region-local restriction w_loc = [[R]] (r / mult) for every coarse node of the level,
+// zero at masked coarse nodes (their column of P is zero). Shared coarse nodes store into
+// y for the coarse interface sum (Psibar^T Psibar).
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kTile)
+k_restrict(Grid Gc, const RegionDev* __restrict__ fregions, const VT* __restrict__ r,
+           const uint8_t* __restrict__ fmult, const uint8_t* __restrict__ cmask,
+           const uint8_t* __restrict__ cmult, VT* __restrict__ w, VT* __restrict__ yc) {
+  RMG_FOR_NODES(Gc)
+    int I, J, L;
+    decode(li, R, I, J, L);
+    VT acc = VT(0);
+    if (!cmask[n]) {
+      const RegionDev F = fregions[tile_.region];
+      const int zlo = DIM == 3 ? -2 : 0, zhi = DIM == 3 ? 2 : 0;
+      for (int c = zlo; c <= zhi; ++c) {
+        const int fz = 3 * L + c;
+        if (fz < 0 || fz >= F.nz) continue;
+        const double wz = DIM == 3 ? w1d(c) : 1.0;
+        for (int b = -2; b <= 2; ++b) {
+          const int fy = 3 * J + b;
+          if (fy < 0 || fy >= F.ny) continue;
+          const double wy = w1d(b);
+          for (int a = -2; a <= 2; ++a) {
+            const int fx = 3 * I + a;
+            if (fx < 0 || fx >= F.nx) continue;
+            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
+            const VT wgt = VT(wz * (wy * w1d(a)));
+            const VT sc = r[f] * (VT(1) / VT(fmult[f]));
+            acc = fma(wgt, sc, acc);
+          }
+        }
+      }
+    }
+    if (cmult[n] > 1) yc[n] = acc; else w[n] = acc;
+  RMG_END_FOR_NODES
+}
+
+// Region-local interpolation and correction u += [[P]] ubar (no inter-region exchange).
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kTile)
+k_prolong(Grid Gf, const RegionDev* __restrict__ cregions, const uint8_t* __restrict__ fmask,
+          const VT* __restrict__ ubar, VT* __restrict__ u) {
+  RMG_FOR_NODES(Gf)
+    if (fmask[n]) continue;
+    int i, j, l;
+    decode(li, R, i, j, l);
+    const RegionDev C = cregions[tile_.region];
+    int cx[2], cy[2], cz[2];
+    double wx[2], wy[2], wz[2];
+    int nxs, nys, nzs;
+    {
+      const int c0 = i / 3, rem = i - 3 * c0;
+      cx[0] = c0; wx[0] = rem ? 1.0 - rem / 3.0 : 1.0; cx[1] = c0 + 1; wx[1] = rem / 3.0;
+      nxs = rem ? 2 : 1;
+    }
+    {
+      const int c0 = j / 3, rem = j - 3 * c0;
+      cy[0] = c0; wy[0] = rem ? 1.0 - rem / 3.0 : 1.0; cy[1] = c0 + 1; wy[1] = rem / 3.0;
+      nys = rem ? 2 : 1;
+    }
+    if (DIM == 3) {
+      const int c0 = l / 3, rem = l - 3 * c0;
+      cz[0] = c0; wz[0] = rem ? 1.0 - rem / 3.0 : 1.0; cz[1] = c0 + 1; wz[1] = rem / 3.0;
+      nzs = rem ? 2 : 1;
+    } else {
+      cz[0] = 0; wz[0] = 1.0; nzs = 1;
+    }
+    VT acc = VT(0);
+    for (int c = 0; c < nzs; ++c)
+      for (int b = 0; b < nys; ++b)
+        for (int a = 0; a < nxs; ++a) {
+          const int k = C.off + cx[a] + C.nx * (cy[b] + C.ny * cz[c]);
+          const VT wgt = VT(wz[c] * (wy[b] * wx[a]));
+          acc = fma(wgt, ubar[k], acc);
+        }
+    u[n] = u[n] + acc;
+  RMG_END_FOR_NODES
+}
+
+// ------------------------------------------------------------------ reductions
+// Deterministic two-pass reductions: every block writes one partial sum; a single block
+// adds the partials in order.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[BS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (ln < BS / 32) ? sh[ln] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;   // valid in thread 0
+}
+
+// Composite inner product of consistent regional vectors: sum x y / mult.
+template <typename XT, typename YT>
+__global__ void __launch_bounds__(256)
+k_dot(int n, const XT* __restrict__ x, const YT* __restrict__ y, const uint8_t* __restrict__ mult,
+      double* __restrict__ partials) {
+  double s = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    s += (double(x[k]) * double(y[k])) * (1.0 / double(mult[k]));
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__device__ __forceinline__ double sum_partials(const double* __restrict__ partials, int np) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) s += partials[k];
+  return block_sum<256>(s);
+}
+
+}  // namespace rmg

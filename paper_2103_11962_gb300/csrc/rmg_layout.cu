@@ -1,0 +1,450 @@
+// Region layout (Psi), non-invasive operator splitting and composite <-> regional maps.
+#include <algorithm>
+#include <climits>
+
+#include "rmg_kernels.cuh"
+#include "rmg_layout.cuh"
+
+namespace rmg {
+
+int persistent_grid(const Ctx& c, int work_items, int per_sm) {
+  const long cap = (long)c.nsm * per_sm;
+  return (int)std::max(1L, std::min<long>(cap, std::max(1, work_items)));
+}
+
+void Ctx::check_device_error(const char* where) {
+  int h = 0;
+  RMG_CUDA(cudaMemcpyAsync(&h, d_err.get(), sizeof(int), cudaMemcpyDeviceToHost, stream));
+  RMG_CUDA(cudaStreamSynchronize(stream));
+  if (h == 0) return;
+  RMG_CUDA(cudaMemsetAsync(d_err.get(), 0, sizeof(int), stream));
+  const char* what = "unknown device error";
+  rmg_status st = RMG_ERR_LAYOUT;
+  switch (h) {
+    case DERR_GID_RANGE: what = "a region gid is outside [0, n_composite)"; break;
+    case DERR_UNCOVERED: what = "a composite node belongs to no region"; break;
+    case DERR_MULT: what = "a composite node has more than 255 regional copies"; break;
+    case DERR_STENCIL: what = "a matrix entry couples nodes that are not stencil neighbours "
+                              "inside a common region"; break;
+    case DERR_COARSE_MISMATCH: what = "co-located nodes disagree on being coarse points "
+                                      "(regions do not coarsen conformingly)"; break;
+    case DERR_NOT_SPD: what = "coarsest composite operator is not positive definite";
+      st = RMG_ERR_SINGULAR; break;
+  }
+  throw Error(st, std::string(where) + ": " + what);
+}
+
+// ------------------------------------------------------------------ scan
+namespace {
+constexpr int kScanBS = 512;
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kScanBS * kScanPer;
+
+__global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out, int n,
+                              int* __restrict__ block_sums) {
+  __shared__ int sh[kScanBS];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int tsum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    tsum += v[k];
+  }
+  sh[threadIdx.x] = tsum;
+  __syncthreads();
+  for (int o = 1; o < kScanBS; o <<= 1) {
+    const int t = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - tsum;   // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanBS - 1) block_sums[blockIdx.x] = sh[kScanBS - 1];
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ offs) {
+  const int base = blockIdx.x * kScanChunk;
+  const int add = offs[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanChunk; k += blockDim.x)
+    if (base + k < n) out[base + k] += add;
+}
+}  // namespace
+
+static void scan_rec(Ctx& c, const int* in, int* out, int n, int* total_dev) {
+  const int nb = (n + kScanChunk - 1) / kScanChunk;
+  DBuf<int> bs(nb + 1), bso(nb + 1);
+  k_scan_blocks<<<nb, kScanBS, 0, c.stream>>>(in, out, n, bs.get());
+  RMG_LAUNCHED();
+  if (nb == 1) {
+    RMG_CUDA(cudaMemcpyAsync(total_dev, bs.get(), sizeof(int), cudaMemcpyDeviceToDevice,
+                             c.stream));
+  } else {
+    scan_rec(c, bs.get(), bso.get(), nb, total_dev);
+    k_scan_add<<<nb, kScanBS, 0, c.stream>>>(out, n, bso.get());
+    RMG_LAUNCHED();
+  }
+  // the temporaries are freed when the stream work that uses them has finished
+  RMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+int exclusive_scan(Ctx& c, const int* in, int* out, int n) {
+  if (n == 0) return 0;
+  DBuf<int> tot(1);
+  scan_rec(c, in, out, n, tot.get());
+  int h = 0;
+  RMG_CUDA(cudaMemcpy(&h, tot.get(), sizeof(int), cudaMemcpyDeviceToHost));
+  return h;
+}
+
+// ------------------------------------------------------------------ layout kernels
+namespace {
+__global__ void k_gids_in(int n_r, const int64_t* __restrict__ g64, int64_t ncomp,
+                          int* __restrict__ gid, int* __restrict__ count, int* err) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x) {
+    const int64_t g = g64[k];
+    if (g < 0 || g >= ncomp) { set_err(err, DERR_GID_RANGE); gid[k] = 0; continue; }
+    gid[k] = (int)g;
+    atomicAdd(&count[g], 1);
+  }
+}
+
+__global__ void k_node_attrs(int n_r, const int* __restrict__ gid, const int* __restrict__ count,
+                             const uint8_t* __restrict__ dir, uint8_t* __restrict__ mult,
+                             uint8_t* __restrict__ mask, int* __restrict__ c2r, int* err) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x) {
+    const int g = gid[k];
+    const int m = count[g];
+    if (m > 255) set_err(err, DERR_MULT);
+    mult[k] = (uint8_t)min(m, 255);
+    mask[k] = dir ? (dir[g] ? 1 : 0) : 0;
+    atomicMin(&c2r[g], k);
+  }
+}
+
+__global__ void k_group_flags(int ncomp, const int* __restrict__ count, int* __restrict__ flag,
+                              int* __restrict__ scount, int* err) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncomp; g += gridDim.x * blockDim.x) {
+    const int m = count[g];
+    if (m == 0) set_err(err, DERR_UNCOVERED);
+    flag[g] = m >= 2 ? 1 : 0;
+    scount[g] = m >= 2 ? m : 0;
+  }
+}
+
+__global__ void k_group_index(int ncomp, const int* __restrict__ count,
+                              const int* __restrict__ gidx, const int* __restrict__ sstart,
+                              int* __restrict__ cgrp, int* __restrict__ gptr, int nslots,
+                              int ngroups) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncomp; g += gridDim.x * blockDim.x) {
+    if (count[g] >= 2) {
+      cgrp[g] = gidx[g];
+      gptr[gidx[g]] = sstart[g];
+    } else {
+      cgrp[g] = -1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) gptr[ngroups] = nslots;
+}
+
+__global__ void k_group_fill(int n_r, const int* __restrict__ gid, const int* __restrict__ cgrp,
+                             const int* __restrict__ gptr, int* __restrict__ fill,
+                             int* __restrict__ gslot) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x) {
+    const int grp = cgrp[gid[k]];
+    if (grp < 0) continue;
+    const int pos = atomicAdd(&fill[grp], 1);
+    gslot[gptr[grp] + pos] = k;
+  }
+}
+
+__global__ void k_group_sort(int ngroups, const int* __restrict__ gptr, int* __restrict__ gslot) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+    const int a = gptr[g], e = gptr[g + 1];
+    for (int p = a + 1; p < e; ++p) {
+      const int v = gslot[p];
+      int q = p - 1;
+      while (q >= a && gslot[q] > v) { gslot[q + 1] = gslot[q]; --q; }
+      gslot[q + 1] = v;
+    }
+  }
+}
+
+__global__ void k_fill_int(int n, int* p, int v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
+}
+}  // namespace
+
+void build_tiles(Level& L) {
+  L.htiles.clear();
+  for (int r = 0; r < L.nreg; ++r) {
+    const int sz = L.hdims[3 * r] * L.hdims[3 * r + 1] * L.hdims[3 * r + 2];
+    for (int s = 0; s < sz; s += kTile) L.htiles.push_back(Tile{r, s});
+  }
+  L.tiles.alloc(L.htiles.size());
+  RMG_CUDA(cudaMemcpy(L.tiles.get(), L.htiles.data(), L.htiles.size() * sizeof(Tile),
+                      cudaMemcpyHostToDevice));
+  std::vector<RegionDev> hr(L.nreg);
+  for (int r = 0; r < L.nreg; ++r)
+    hr[r] = RegionDev{L.hdims[3 * r], L.hdims[3 * r + 1], L.hdims[3 * r + 2], 0, L.hoff[r]};
+  L.regions.alloc(L.nreg);
+  RMG_CUDA(cudaMemcpy(L.regions.get(), hr.data(), hr.size() * sizeof(RegionDev),
+                      cudaMemcpyHostToDevice));
+}
+
+void set_geometry(Level& L, int dim, int nreg, const int* dims) {
+  L.dim = dim;
+  L.nreg = nreg;
+  L.hdims.assign(dims, dims + 3 * nreg);
+  L.hoff.assign(nreg + 1, 0);
+  long long tot = 0;
+  for (int r = 0; r < nreg; ++r) {
+    const long long sz = (long long)dims[3 * r] * dims[3 * r + 1] * dims[3 * r + 2];
+    L.hoff[r] = (int)tot;
+    tot += sz;
+    RMG_REQUIRE(tot < INT_MAX, RMG_ERR_ARG, "more than 2^31-1 regional nodes");
+  }
+  L.hoff[nreg] = (int)tot;
+  L.n_r = (int)tot;
+  build_tiles(L);
+}
+
+// Multiplicities, masks, composite -> regional maps and interface groups of a level whose
+// gid array (int) is already on the device. `dir` is a composite-indexed mask or NULL;
+// `rmask` (regional) may be given instead.
+void build_groups(Ctx& c, Level& L, const uint8_t* dir_comp, const uint8_t* rmask,
+                  DBuf<int>& count) {
+  const int n_r = L.n_r, nc = L.ncomp;
+  const int gb = persistent_grid(c, (n_r + 255) / 256), gc = persistent_grid(c, (nc + 255) / 256);
+  L.mult.alloc(n_r);
+  L.mask.alloc(n_r);
+  L.c2r.alloc(nc);
+  k_fill_int<<<gc, 256, 0, c.stream>>>(nc, L.c2r.get(), INT_MAX);
+  RMG_LAUNCHED();
+  k_node_attrs<<<gb, 256, 0, c.stream>>>(n_r, L.gid.get(), count.get(), dir_comp, L.mult.get(),
+                                         L.mask.get(), L.c2r.get(), c.d_err.get());
+  RMG_LAUNCHED();
+  if (rmask)
+    RMG_CUDA(cudaMemcpyAsync(L.mask.get(), rmask, n_r, cudaMemcpyDeviceToDevice, c.stream));
+  DBuf<int> flag(nc), scount(nc), gidx(nc), sstart(nc);
+  k_group_flags<<<gc, 256, 0, c.stream>>>(nc, count.get(), flag.get(), scount.get(),
+                                          c.d_err.get());
+  RMG_LAUNCHED();
+  L.ngroups = exclusive_scan(c, flag.get(), gidx.get(), nc);
+  L.nslots = exclusive_scan(c, scount.get(), sstart.get(), nc);
+  L.cgrp.alloc(nc);
+  L.gptr.alloc(L.ngroups + 1);
+  L.gslot.alloc(std::max(1, L.nslots));
+  k_group_index<<<gc, 256, 0, c.stream>>>(nc, count.get(), gidx.get(), sstart.get(),
+                                          L.cgrp.get(), L.gptr.get(), L.nslots, L.ngroups);
+  RMG_LAUNCHED();
+  DBuf<int> fill(std::max(1, L.ngroups));
+  RMG_CUDA(cudaMemsetAsync(fill.get(), 0, fill.bytes(), c.stream));
+  k_group_fill<<<gb, 256, 0, c.stream>>>(n_r, L.gid.get(), L.cgrp.get(), L.gptr.get(),
+                                         fill.get(), L.gslot.get());
+  RMG_LAUNCHED();
+  if (L.ngroups) {
+    k_group_sort<<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
+        L.ngroups, L.gptr.get(), L.gslot.get());
+    RMG_LAUNCHED();
+  }
+  RMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void layout_create(Ctx& c, Level& L, int dim, int nreg, const int* dims, const int64_t* g64,
+                   int64_t ncomp, const uint8_t* dir) {
+  RMG_REQUIRE(dim == 2 || dim == 3, RMG_ERR_ARG, "dim must be 2 or 3");
+  RMG_REQUIRE(nreg > 0 && dims && g64, RMG_ERR_ARG, "regions, dims and gids are required");
+  RMG_REQUIRE(ncomp > 0 && ncomp < INT_MAX, RMG_ERR_ARG, "n_composite out of range");
+  for (int r = 0; r < nreg; ++r) {
+    RMG_REQUIRE(dims[3 * r] >= 1 && dims[3 * r + 1] >= 1 && dims[3 * r + 2] >= 1, RMG_ERR_ARG,
+                "region dims must be positive");
+    if (dim == 2) RMG_REQUIRE(dims[3 * r + 2] == 1, RMG_ERR_ARG, "2D regions need nz = 1");
+  }
+  set_geometry(L, dim, nreg, dims);
+  L.ncomp = (int)ncomp;
+  L.gid.alloc(L.n_r);
+  DBuf<int> count(L.ncomp);
+  RMG_CUDA(cudaMemsetAsync(count.get(), 0, count.bytes(), c.stream));
+  k_gids_in<<<persistent_grid(c, (L.n_r + 255) / 256), 256, 0, c.stream>>>(
+      L.n_r, g64, ncomp, L.gid.get(), count.get(), c.d_err.get());
+  RMG_LAUNCHED();
+  build_groups(c, L, dir, nullptr, count);
+  c.check_device_error("rmg_layout_create");
+}
+
+// ------------------------------------------------------------------ splitting (Sec. 4)
+namespace {
+// Regional slot of composite node cg inside region k, or -1.
+__device__ __forceinline__ int copy_in_region(int cg, const RegionDev& R, int nodes,
+                                              const int* __restrict__ c2r,
+                                              const int* __restrict__ cgrp,
+                                              const int* __restrict__ gptr,
+                                              const int* __restrict__ gslot) {
+  const int grp = cgrp[cg];
+  if (grp < 0) {
+    const int s = c2r[cg];
+    return (s >= R.off && s < R.off + nodes) ? s : -1;
+  }
+  for (int q = gptr[grp]; q < gptr[grp + 1]; ++q) {
+    const int s = gslot[q];
+    if (s >= R.off && s < R.off + nodes) return s;
+  }
+  return -1;
+}
+
+// Number of regions holding both composite nodes a and b (both shared, or one not).
+__device__ __forceinline__ int share_count(int a, int b, const RegionDev* __restrict__ regs,
+                                           int nreg, const int* __restrict__ cgrp,
+                                           const int* __restrict__ gptr,
+                                           const int* __restrict__ gslot) {
+  const int ga = cgrp[a], gb = cgrp[b];
+  if (ga < 0 || gb < 0) return 1;
+  int q = 0;
+  for (int p = gptr[ga]; p < gptr[ga + 1]; ++p) {
+    const int ra = region_of(regs, nreg, gslot[p]);
+    for (int s = gptr[gb]; s < gptr[gb + 1]; ++s)
+      if (region_of(regs, nreg, gslot[s]) == ra) { ++q; break; }
+  }
+  return q;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTile)
+k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
+            const int* __restrict__ c2r, const int* __restrict__ cgrp,
+            const int* __restrict__ gptr, const int* __restrict__ gslot,
+            const int64_t* __restrict__ rowptr, const int64_t* __restrict__ col,
+            const double* __restrict__ val, int ncomp, double* __restrict__ coef, int* err) {
+  using S = Sten<KIND>;
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    decode(li, R, i, j, l);
+    const int nodes = R.nx * R.ny * R.nz;
+    const int g = gid[n];
+    double acc[S::S];
+#pragma unroll
+    for (int s = 0; s < S::S; ++s) acc[s] = 0.0;
+    double zsum = 0.0, offsum = 0.0;
+    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+      const int64_t c64 = col[e];
+      const double v = val[e];
+      if (c64 < 0 || c64 >= ncomp) { set_err(err, DERR_GID_RANGE); continue; }
+      const int c = (int)c64;
+      zsum += v;
+      if (c == g) continue;
+      const int sc = copy_in_region(c, R, nodes, c2r, cgrp, gptr, gslot);
+      if (sc < 0) continue;                      // entry belongs to other regions only
+      int ic, jc, lc;
+      decode(sc - R.off, R, ic, jc, lc);
+      const int slot = sten_slot<KIND>(ic - i, jc - j, lc - l);
+      if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
+      const int q = share_count(g, c, G.regions, G.nreg, cgrp, gptr, gslot);
+      const double vs = v / (double)q;
+      offsum += vs;
+#pragma unroll
+      for (int s = 0; s < S::S; ++s)
+        if (s == slot) acc[s] += vs;
+    }
+    acc[S::CENTER] = zsum / (double)mult[n] - offsum;
+#pragma unroll
+    for (int s = 0; s < S::S; ++s) coef[(size_t)s * G.n_r + n] = acc[s];
+  RMG_END_FOR_NODES
+}
+
+__global__ void k_comp_to_reg(int n_r, const int* __restrict__ gid, const double* __restrict__ c,
+                              double* __restrict__ r) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
+    r[k] = c[gid[k]];
+}
+
+__global__ void k_comp_to_reg_masked(int n_r, const int* __restrict__ gid,
+                                     const uint8_t* __restrict__ mask,
+                                     const double* __restrict__ c, double* __restrict__ r) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
+    r[k] = mask[k] ? 0.0 : c[gid[k]];
+}
+
+__global__ void k_reg_to_comp(int ncomp, const int* __restrict__ c2r, const int* __restrict__ cgrp,
+                              const int* __restrict__ gptr, const int* __restrict__ gslot,
+                              const double* __restrict__ r, double* __restrict__ c, int average) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncomp; g += gridDim.x * blockDim.x) {
+    const int grp = cgrp[g];
+    if (grp < 0) { c[g] = r[c2r[g]]; continue; }
+    double s = 0.0;
+    const int a = gptr[grp], e = gptr[grp + 1];
+    for (int q = a; q < e; ++q) s += r[gslot[q]];
+    c[g] = average ? s / (double)(e - a) : s;
+  }
+}
+}  // namespace
+
+void split_from_csr(Ctx& c, Level& L, int kind, const int64_t* rowptr, const int64_t* col,
+                    const double* val) {
+  RMG_REQUIRE(rowptr && col && val, RMG_ERR_ARG, "CSR arrays are required");
+  RMG_REQUIRE((L.dim == 2 && (kind == 5 || kind == 9)) || (L.dim == 3 && (kind == 7 || kind == 27)),
+              RMG_ERR_ARG, "stencil must be 5/9 in 2D and 7/27 in 3D");
+  L.kind = kind;
+  L.coef.alloc((size_t)kind * L.n_r);
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+#define RMG_SPLIT(K)                                                                        \
+  k_split_csr<K><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(),     \
+                                             L.cgrp.get(), L.gptr.get(), L.gslot.get(),      \
+                                             rowptr, col, val, L.ncomp, L.coef.get(),    \
+                                             c.d_err.get())
+  switch (kind) {
+    case 5: RMG_SPLIT(5); break;
+    case 7: RMG_SPLIT(7); break;
+    case 9: RMG_SPLIT(9); break;
+    default: RMG_SPLIT(27); break;
+  }
+#undef RMG_SPLIT
+  RMG_LAUNCHED();
+  c.check_device_error("rmg_operator_from_csr");
+}
+
+void comp_to_reg(Ctx& c, const Level& L, const double* comp, double* reg, bool zero_masked) {
+  const int gb = persistent_grid(c, (L.n_r + 255) / 256);
+  if (zero_masked)
+    k_comp_to_reg_masked<<<gb, 256, 0, c.stream>>>(L.n_r, L.gid.get(), L.mask.get(), comp, reg);
+  else
+    k_comp_to_reg<<<gb, 256, 0, c.stream>>>(L.n_r, L.gid.get(), comp, reg);
+  RMG_LAUNCHED();
+}
+
+void reg_to_comp(Ctx& c, const Level& L, const double* reg, double* comp, int average) {
+  k_reg_to_comp<<<persistent_grid(c, (L.ncomp + 255) / 256), 256, 0, c.stream>>>(
+      L.ncomp, L.c2r.get(), L.cgrp.get(), L.gptr.get(), L.gslot.get(), reg, comp, average);
+  RMG_LAUNCHED();
+}
+
+// y = Psi^T Psi [[A]] u in FP64 with the level's FP64 coefficients.
+void regional_apply(Ctx& c, const Level& L, const double* u, double* y, double* ypart) {
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+  EpiStore<double> epi{y};
+#define RMG_APPLY(K)                                                                       \
+  k_stencil<K, double, double, double><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), u,      \
+                                                                   L.mult.get(), ypart, epi)
+  switch (L.kind) {
+    case 5: RMG_APPLY(5); break;
+    case 7: RMG_APPLY(7); break;
+    case 9: RMG_APPLY(9); break;
+    default: RMG_APPLY(27); break;
+  }
+#undef RMG_APPLY
+  RMG_LAUNCHED();
+  if (L.ngroups) {
+    k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
+        L.ngroups, L.gptr.get(), L.gslot.get(), ypart, epi);
+    RMG_LAUNCHED();
+  }
+}
+
+}  // namespace rmg

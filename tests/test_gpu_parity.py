@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (fixed for the plain FP64 path): every operator apply and every setup product to
+1e-12 relative to the largest entry; V-cycle iterates to 1e-10 relative; identical PCG
+iteration counts.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import matrix_rel_diff, rel_max, stencils_to_matrix
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+OP_TOL = 1e-12
+CYCLE_TOL = 1e-10
+
+CASES = {
+    # name: (factory, levels)
+    "c1_poisson2d": (lambda: W.config("c1_poisson2d"), 4),
+    "poisson2d_uneven": (lambda: W.poisson2d_5pt(region_grid=(3, 2), n=28, seed=11), 3),
+    "q1_2d": (lambda: W.q1_laplace2d(region_grid=(2, 3), n=19, seed=12), 3),
+    "diff3d_small": (lambda: W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28),
+                                               seed=5), 3),
+    "q1_3d_small": (lambda: W.q1_laplace3d(region_grid=(2, 2, 1), n=19, seed=6), 3),
+    "single_region": (lambda: W.diffusion3d_7pt(region_grid=(1, 1, 1), choices=(28,), seed=7), 3),
+    "highcontrast_small": (lambda: W.highcontrast3d_7pt(region_grid=(3, 2, 2), choices=(10, 19),
+                                                        seed=13), 3),
+}
+
+_cache = {}
+
+
+def _problem(name):
+    if name not in _cache:
+        f, nlev = CASES[name]
+        _cache[name] = (f(), nlev)
+    return _cache[name]
+
+
+def _oracle(name, smoother):
+    from oracle import cycle, hierarchy
+    key = ("oracle", name, smoother)
+    if key not in _cache:
+        p, nlev = _problem(name)
+        levels = hierarchy.build(p, nlev)
+        opts = _oracle_opts(smoother)
+        mg = cycle.RegionalMG(levels, opts)
+        _cache[key] = (levels, mg, opts)
+    return _cache[key]
+
+
+def _oracle_opts(smoother):
+    from oracle import cycle
+    if smoother == "jacobi":
+        return cycle.Options(smoother="jacobi", nu1=2, nu2=2, omega=0.67)
+    return cycle.Options(smoother="chebyshev", nu1=1, nu2=1, degree=3)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2103_11962_gb300 import rmg
+    return rmg.Context(0)
+
+
+def _gpu(ctx, name, smoother, precision=0, use_graph=1):
+    from paper_2103_11962_gb300 import rmg, upload
+    p, nlev = _problem(name)
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    o = rmg.default_options(levels=nlev, use_graph=use_graph, precision=precision)
+    if smoother == "jacobi":
+        o.smoother, o.nu1, o.nu2, o.omega = rmg.JACOBI, 2, 2, 0.67
+    else:
+        o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, 1, 1, 3
+    h = rmg.Hierarchy(lay, o)
+    return p, dp, lay, h
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_layout_and_split(ctx, name):
+    from oracle.split import split_regional
+    p, dp, lay, h = _gpu(ctx, name, "jacobi")
+    levels, _, _ = _oracle(name, "jacobi")
+    L0 = levels[0].layout
+    sz = lay.sizes()
+    assert sz["n_regional"] == L0.n_r and sz["n_composite"] == p.n_nodes
+    assert sz["n_groups"] == int((L0.mult > 1).sum())
+    assert sz["n_group_slots"] == int(L0.mult[L0.mult > 1].sum())
+    n_r, _, kind = h.level_sizes(0)
+    coef = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
+    h.level_export(0, coeffs=coef)
+    M = stencils_to_matrix(p.region_dims, coef.cpu().numpy(), kind)
+    assert matrix_rel_diff(M, levels[0].Ar) <= OP_TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_regional_apply_equals_composite(ctx, name):
+    """Psi^T Psi [[A]] Psi^T x = Psi^T (A x) on the GPU (eq. regional residual)."""
+    p, dp, lay, h = _gpu(ctx, name, "jacobi")
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(p.n_nodes)
+    xd = torch.from_numpy(x).cuda()
+    n_r = lay.sizes()["n_regional"]
+    xr = torch.empty(n_r, dtype=torch.float64, device="cuda")
+    yr = torch.empty_like(xr)
+    lay.comp_to_reg(xd, xr)
+    lay.regional_apply(xr, yr)
+    yc = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+    lay.reg_to_comp(yr, yc, average=True)
+    expect = p.A @ x
+    assert rel_max(yc.cpu().numpy(), expect) <= OP_TOL
+    # consistency: every copy of a shared node holds the same value
+    from oracle.regions import make_layout
+    L0 = make_layout(p.region_dims, p.region_gids, p.n_nodes, p.dirichlet)
+    y = yr.cpu().numpy()
+    assert rel_max(y, L0.to_regional(expect)) <= OP_TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hierarchy_operators(ctx, name):
+    """Every level's [[Abar]] (regional Galerkin product) and D~^-1 against the oracle."""
+    p, dp, lay, h = _gpu(ctx, name, "jacobi")
+    levels, _, _ = _oracle(name, "jacobi")
+    for l, lev in enumerate(levels):
+        n_r, ncomp, kind = h.level_sizes(l)
+        assert n_r == lev.layout.n_r and ncomp == lev.layout.n
+        coef = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
+        dinv = torch.empty(n_r, dtype=torch.float64, device="cuda")
+        gids = torch.empty(n_r, dtype=torch.int64, device="cuda")
+        h.level_export(l, coeffs=coef, dinv=dinv, gids=gids)
+        assert np.array_equal(gids.cpu().numpy(), lev.layout.region_gids)
+        M = stencils_to_matrix(lev.layout.region_dims, coef.cpu().numpy(), kind)
+        assert matrix_rel_diff(M, lev.Ar) <= OP_TOL, f"level {l}"
+        assert rel_max(dinv.cpu().numpy(), lev.Dinv_r) <= OP_TOL
+
+
+@pytest.mark.parametrize("name", ["c1_poisson2d", "diff3d_small", "q1_3d_small"])
+def test_coarse_composite_matrix(ctx, name):
+    from oracle import hierarchy
+    p, dp, lay, h = _gpu(ctx, name, "jacobi")
+    levels, mg, _ = _oracle(name, "jacobi")
+    dense, ids = h.coarse_matrix()
+    last = levels[-1]
+    free = np.flatnonzero(~last.layout.mask)
+    assert np.array_equal(ids, free)
+    Abar = hierarchy.coarse_composite_from_regional(last).toarray()[np.ix_(free, free)]
+    assert rel_max(dense, Abar) <= OP_TOL
+
+
+@pytest.mark.parametrize("name", ["c1_poisson2d", "diff3d_small", "q1_2d", "highcontrast_small"])
+def test_power_method_lambda(ctx, name):
+    p, dp, lay, h = _gpu(ctx, name, "chebyshev")
+    levels, mg, _ = _oracle(name, "chebyshev")
+    for l in range(len(levels) - 1):
+        assert h.lam(l) == pytest.approx(levels[l].lam_r, rel=1e-12)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_matches_oracle(ctx, name, smoother, use_graph):
+    p, dp, lay, h = _gpu(ctx, name, smoother, use_graph=use_graph)
+    levels, mg, _ = _oracle(name, smoother)
+    L0 = levels[0].layout
+    z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+    h.vcycle(dp.b, z)
+    expect = L0.average_to_composite(mg.precondition(L0.to_regional(p.b)))
+    assert rel_max(z.cpu().numpy(), expect) <= CYCLE_TOL
+    # a second application on another right-hand side (graph replay, buffers reused)
+    r2 = np.random.default_rng(9).uniform(-1, 1, p.n_nodes)
+    r2[p.dirichlet.astype(bool)] = 0
+    h.vcycle(torch.from_numpy(r2).cuda(), z)
+    expect2 = L0.average_to_composite(mg.precondition(L0.to_regional(r2)))
+    assert rel_max(z.cpu().numpy(), expect2) <= CYCLE_TOL
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("name", ["c1_poisson2d", "diff3d_small", "q1_3d_small",
+                                  "highcontrast_small", "single_region"])
+def test_pcg_matches_oracle(ctx, name, smoother):
+    from oracle import krylov
+    p, dp, lay, h = _gpu(ctx, name, smoother)
+    levels, mg, _ = _oracle(name, smoother)
+    x_or, it_or, hist_or = krylov.pcg(p.A, p.b, krylov.regional_preconditioner(mg), rtol=1e-10)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    res = h.pcg(dp.b, x, rtol=1e-10, maxit=200)
+    assert res["converged"]
+    assert res["iterations"] == it_or
+    assert res["true_relres"] <= 1.5e-10
+    assert rel_max(res["history"], np.asarray(hist_or)) <= 1e-6
+    xo = x.cpu().numpy()
+    assert np.linalg.norm(xo - x_or) <= 1e-8 * np.linalg.norm(x_or)
+
+
+def test_setup_numeric_refresh(ctx):
+    """New coefficients on the same mesh: the numeric setup and the captured graph follow."""
+    from oracle import cycle, hierarchy
+    from paper_2103_11962_gb300 import upload
+    name = "diff3d_small"
+    p, dp, lay, h = _gpu(ctx, name, "chebyshev")
+    p2 = W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=5, sigma=0.5)
+    assert p2.global_dims == p.global_dims
+    d2 = upload(p2)
+    lay.operator_from_csr(p2.stencil, d2.rowptr, d2.col, d2.val)
+    h.setup_numeric()
+    levels = hierarchy.build(p2, 3)
+    mg = cycle.RegionalMG(levels, _oracle_opts("chebyshev"))
+    L0 = levels[0].layout
+    z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+    h.vcycle(d2.b, z)
+    expect = L0.average_to_composite(mg.precondition(L0.to_regional(p2.b)))
+    assert rel_max(z.cpu().numpy(), expect) <= CYCLE_TOL
+
+
+def test_errors_are_reported(ctx):
+    from paper_2103_11962_gb300 import rmg
+    p = W.diffusion3d_7pt(region_grid=(2, 1, 1), choices=(10,), seed=1)
+    gids = torch.from_numpy(p.region_gids.copy()).cuda()
+    gids[5] = p.n_nodes + 3          # out of range
+    with pytest.raises(rmg.RmgError) as e:
+        rmg.Layout(ctx, 3, p.region_dims, gids, p.n_nodes, None)
+    assert e.value.status == 2
+    # region sizes that cannot be coarsened 3:1 are rejected at setup
+    p = W.diffusion3d_7pt(region_grid=(2, 1, 1), choices=(9,), seed=1)
+    from paper_2103_11962_gb300 import upload
+    dp = upload(p)
+    lay = rmg.Layout(ctx, 3, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(7, dp.rowptr, dp.col, dp.val)
+    with pytest.raises(rmg.RmgError) as e:
+        rmg.Hierarchy(lay, rmg.default_options(levels=2))
+    assert e.value.status == 2
+    # a 27-point matrix declared as 7-point fails the split
+    q = W.q1_laplace3d(region_grid=(1, 1, 1), n=10)
+    dq = upload(q)
+    lay = rmg.Layout(ctx, 3, q.region_dims, dq.gids, q.n_nodes, dq.dirichlet)
+    with pytest.raises(rmg.RmgError) as e:
+        lay.operator_from_csr(7, dq.rowptr, dq.col, dq.val)
+    assert e.value.status == 2
+    # the context is still usable
+    lay.operator_from_csr(27, dq.rowptr, dq.col, dq.val)
