@@ -1,0 +1,423 @@
+"""Benchmark: region multigrid preconditioned CG to a 1e-10 relative residual.
+
+One step = one linear system solved from device-resident inputs through the C ABI:
+non-invasive split of the composite CSR matrix into region stencils, numeric hierarchy setup
+(diagonals, regional Galerkin products, Chebyshev power method, coarsest Cholesky and inverse)
+and FP64 PCG with one regional V-cycle per iteration. The mesh (region layout, interface groups)
+and the hierarchy's buffers and CUDA graph are built once before timing.
+
+Metric: V-cycle DOF/s = unknowns x V-cycles of the step / step time (whole step, setup
+included), and the time to the 1e-10 relative residual.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+       [--workload c2_diffusion3d] [--precision fp64|fp32|bf16] [--no-mixed] [--no-e2e] [--no-cpu]
+Under torchrun every rank solves its own copy of the system (independent problems, no
+collective on the data path; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle DOF/s & time to 1e-10 rel. residual, mixed/learned vs plain FP64"
+RTOL = 1e-10
+
+# Per-node algorithmic bytes and FP64 flops of the timed kernel, the fine-level Chebyshev
+# recurrence sweep with a 7-point stencil (k_stencil<7, EpiCheb>): 7 coefficients, u, b,
+# D~^-1, d read; d and u_out written; 1-byte multiplicity read.
+SWEEP_BYTES = {("fp64", 7): 7 * 8 + 4 * 8 + 2 * 8 + 1,
+               ("fp32", 7): 7 * 4 + 4 * 4 + 2 * 4 + 1,
+               ("bf16", 7): 7 * 2 + 4 * 4 + 2 * 4 + 1}
+SWEEP_FLOPS = {7: 2 * 7 + 6}
+
+WORKLOADS = {
+    "c2_diffusion3d": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                           desc="3D 7-point variable-coefficient diffusion, 8x8x4 regions with "
+                                "per-axis node counts from {28,55,82} (seed 1), log-normal "
+                                "per-element kappa (sigma 1), Chebyshev degree 3, 4 levels"),
+    "c1_poisson2d": dict(levels=4, smoother="jacobi", nu1=2, nu2=2, omega=0.67,
+                         desc="2D Poisson 5-point, 2x2 regions of 82x82, Jacobi 0.67, nu 2/2, "
+                              "4 levels"),
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "src": "fallback"}
+    if os.path.exists(p):
+        d = json.load(open(p))
+        out = {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured",
+               "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))}
+    # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (measured 1.196 TFLOP/s
+    # with dependent-free FMA chains at 1995 MHz on this part).
+    out["fp64_tflops"] = 152 * 2 * 2 * out.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return out
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ oracle leg
+def oracle_sample_cmd(workload, seconds_budget=20.0):
+    """Command that runs the CPU oracle pipeline (split, hierarchy, PCG to 1e-10) on a bounded
+    sample of the workload and prints a JSON summary. Single-threaded BLAS."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads as W
+from oracle import cycle, hierarchy, krylov
+w = {workload!r}
+if w == 'c2_diffusion3d':
+    p = W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(28, 55, 82), seed=1)
+    o = cycle.Options(smoother='chebyshev', nu1=1, nu2=1, degree=3)
+    sample = 'C2-shaped 2x2x2-region instance (slabs from {{28,55,82}}, seed 1, log-normal kappa)'
+else:
+    p = W.config('c1_poisson2d')
+    o = cycle.Options(smoother='jacobi', nu1=2, nu2=2, omega=0.67)
+    sample = 'full C1 workload'
+t0 = time.perf_counter()
+levels = hierarchy.build(p, 4)
+mg = cycle.RegionalMG(levels, o)
+x, it, hist = krylov.pcg(p.A, p.b, krylov.regional_preconditioner(mg), rtol={RTOL})
+t1 = time.perf_counter()
+ncyc = it if hist[-1] <= {RTOL} else it + 1
+print(json.dumps(dict(seconds=t1 - t0, iterations=it, vcycles=ncyc, unknowns=p.n_unknowns,
+                      n_regional=p.n_regional_nodes, sample=sample)))
+"""
+    return [sys.executable, "-c", code]
+
+
+def run_oracle_sample(workload):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    res = subprocess.run(oracle_sample_cmd(workload), capture_output=True, text=True, env=env,
+                         timeout=900)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    d["value"] = d["unknowns"] * d["vcycles"] / d["seconds"]
+    return d
+
+
+# ------------------------------------------------------------------------------ native leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c2_diffusion3d", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reference_arm(args, cfg)
+        return
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2103_11962_gb300 import rmg, upload
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local_rank}"
+
+    p = W.config(args.workload)
+    dp = upload(p, dev)
+    stream = torch.cuda.current_stream(local_rank)
+    ctx = rmg.Context(local_rank, stream.cuda_stream)
+    t_lay = time.perf_counter()
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    t_lay = time.perf_counter() - t_lay
+
+    def options(prec):
+        o = rmg.default_options(levels=cfg["levels"], precision={"fp64": rmg.FP64,
+                                                                "fp32": rmg.FP32,
+                                                                "bf16": rmg.FP32_BF16COEF}[prec])
+        if cfg["smoother"] == "chebyshev":
+            o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, cfg["nu1"], cfg["nu2"], cfg["degree"]
+        else:
+            o.smoother, o.nu1, o.nu2, o.omega = rmg.JACOBI, cfg["nu1"], cfg["nu2"], cfg["omega"]
+        return o
+
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    hier = rmg.Hierarchy(lay, options(args.precision))
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device=dev)
+
+    def step(h):
+        lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+        h.setup_numeric()
+        x.zero_()
+        return h.pcg(dp.b, x, rtol=RTOL, maxit=500, history=False)
+
+    def timed(h, K, W_, e2e=None):
+        for _ in range(W_):
+            (e2e or step)(h)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        h.probe(reset=True)
+        l0 = rmg.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        infos = [(e2e or step)(h) for _ in range(K)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = rmg.launch_count() - l0
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, infos, launches, h.probe(reset=True)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms, infos, launches, (probe_ms, probe_n) = timed(hier, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_step = ms / args.steps
+    info = infos[-1]
+    ncyc = info["vcycles"]
+    units = p.n_unknowns * ncyc * args.steps * world
+    value = units / (ms / 1e3)
+
+    # per-phase breakdown of one step (outside the timed region)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream); lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    e[1].record(stream); hier.setup_numeric()
+    e[2].record(stream); x.zero_(); bi = hier.pcg(dp.b, x, rtol=RTOL, maxit=500, history=False)
+    e[3].record(stream); torch.cuda.synchronize()
+    breakdown = dict(split_ms=e[0].elapsed_time(e[1]), setup_ms=e[1].elapsed_time(e[2]),
+                     solve_ms=e[2].elapsed_time(e[3]), layout_ms_once=t_lay * 1e3,
+                     vcycle_launches=hier.vcycle_launches())
+    # V-cycle alone (graph replays), for the per-cycle figure
+    r = dp.b.clone()
+    z = torch.empty_like(r)
+    for _ in range(3):
+        hier.vcycle(r, z)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    nrep = 20
+    for _ in range(nrep):
+        hier.vcycle(r, z)
+    e[1].record(stream); torch.cuda.synchronize()
+    vc_ms = e[0].elapsed_time(e[1]) / nrep
+    breakdown["vcycle_ms"] = vc_ms
+    breakdown["vcycle_dof_per_s"] = p.n_unknowns / (vc_ms / 1e3)
+
+    pk = peaks()
+    kern_ms = probe_ms / max(1, probe_n)
+    n_r0 = p.n_regional_nodes
+    prec = args.precision
+    bytes_launch = SWEEP_BYTES[(prec, 7)] * n_r0 if p.stencil == 7 else None
+    flops_launch = SWEEP_FLOPS.get(p.stencil, 0) * n_r0
+    roofline = None
+    if bytes_launch and kern_ms > 0:
+        gbs = bytes_launch / (kern_ms / 1e3) / 1e9
+        tfl = flops_launch / (kern_ms / 1e3) / 1e12
+        hbm_frac = gbs / pk["hbm_gbs"]
+        alu_frac = tfl / pk["fp64_tflops"] if prec == "fp64" else 0.0
+        if prec == "fp64" and alu_frac > hbm_frac:
+            roofline = dict(bound="alu", achieved=round(tfl, 4), peak=round(pk["fp64_tflops"], 4),
+                            unit="TFLOP/s (FP64)", frac=round(alu_frac, 4),
+                            hbm=dict(achieved=round(gbs, 1), peak=pk["hbm_gbs"],
+                                     unit="GB/s", frac=round(hbm_frac, 4),
+                                     peak_src=pk["src"]),
+                            peak_src="derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock")
+        else:
+            roofline = dict(bound="hbm", achieved=round(gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
+                            frac=round(hbm_frac, 4), peak_src=pk["src"])
+        roofline.update(kernel=f"k_stencil<{p.stencil}, EpiCheb> level 0 ({prec})",
+                        traffic=None, ms_per_launch=round(kern_ms, 4),
+                        launches_timed=probe_n, bytes_per_launch=bytes_launch,
+                        flops_per_launch=flops_launch)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "DOF*V-cycles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 cycle + f64 CG", "bf16": "f32/bf16 cycle + f64 CG"}[prec],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": cfg["desc"],
+                   "global_dims": list(p.global_dims), "regions": int(p.nregions),
+                   "unknowns": p.n_unknowns, "regional_nodes": p.n_regional_nodes,
+                   "composite_nnz": int(p.A.nnz), "levels": cfg["levels"],
+                   "precision": prec, "rtol": RTOL,
+                   "l2": "inputs larger than L2 (31.7M-node vectors, 1.8 GB stencils)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "time_to_tol_s": ms_step / 1e3,
+        "pcg_iterations": info["iterations"],
+        "vcycles_per_step": ncyc,
+        "true_relres": info["true_relres"],
+        "breakdown": breakdown,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+
+    # mixed-precision V-cycle on the same workload (same 1e-10 FP64 residual)
+    if not args.no_mixed and prec == "fp64":
+        mixed = {}
+        for mp in ("fp32", "bf16"):
+            hm = rmg.Hierarchy(lay, options(mp))
+            msm, infm, _, (pms, pn) = timed(hm, args.steps, args.warmup)
+            im = infm[-1]
+            km = pms / max(1, pn)
+            bl = SWEEP_BYTES[(mp, 7)] * n_r0 if p.stencil == 7 else None
+            mixed[mp] = dict(ms_per_step=msm / args.steps,
+                             value=p.n_unknowns * im["vcycles"] * args.steps * world / (msm / 1e3),
+                             pcg_iterations=im["iterations"], true_relres=im["true_relres"],
+                             kernel_ms=km,
+                             kernel_hbm_frac=(bl / (km / 1e3) / 1e9 / pk["hbm_gbs"]) if bl and km else None,
+                             speedup_vs_fp64=ms_step / (msm / args.steps))
+            hm.close()
+        out["mixed"] = mixed
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs (composite
+    # CSR + right-hand side) from pinned memory, the step, D2H of the solution
+    if not args.no_e2e:
+        hp = {k: getattr(dp, k).cpu().pin_memory() for k in ("rowptr", "col", "val", "b")}
+        hx = torch.empty(p.n_nodes, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in hp.values())
+        d2h = hx.numel() * hx.element_size()
+
+        def e2e_step(h):
+            for k, t in hp.items():
+                getattr(dp, k).copy_(t, non_blocking=True)
+            res = step(h)
+            hx.copy_(x, non_blocking=True)
+            return res
+
+        mse, infe, _, _ = timed(hier, args.steps, args.warmup, e2e=e2e_step)
+        out["e2e"] = {"value": p.n_unknowns * infe[-1]["vcycles"] * args.steps * world / (mse / 1e3),
+                      "unit": "DOF*V-cycles/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": mse / args.steps}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cb = run_oracle_sample(args.workload)
+            out["cpu_baseline"] = {"value": cb["value"], "unit": "DOF*V-cycles/s", "cores": 1,
+                                   "kind": "oracle", "sample": cb["sample"],
+                                   "seconds": cb["seconds"], "iterations": cb["iterations"],
+                                   "unknowns": cb["unknowns"]}
+        except Exception as ex:  # the baseline is reported, not required
+            out["cpu_baseline"] = {"value": None, "unit": "DOF*V-cycles/s", "cores": 1,
+                                   "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, cfg):
+    """The CPU oracle as it stands, timed on the host cores (bounded samples per step)."""
+    samples = []
+    for _ in range(args.warmup):
+        run_oracle_sample(args.workload)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(run_oracle_sample(args.workload))
+    t1 = time.perf_counter()
+    units = sum(s["unknowns"] * s["vcycles"] for s in samples)
+    value = units / sum(s["seconds"] for s in samples)
+    out = {"metric": METRIC, "value": value, "unit": "DOF*V-cycles/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": (t1 - t0) * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "desc": cfg["desc"],
+                      "sample": samples[-1]["sample"]},
+           "cpu_baseline": {"value": value, "unit": "DOF*V-cycles/s", "cores": 1,
+                            "kind": "oracle", "sample": samples[-1]["sample"]},
+           "e2e": {"value": value, "unit": "DOF*V-cycles/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,15 @@ rmg_status rmg_hier_lambda(rmg_hier* hier, int level, double* lam);
 /* Coarsest composite matrix restricted to unmasked nodes (dense, row-major, host double
  * [nc*nc]) and the composite ids of those unknowns (host int64[nc]). Pass NULL to query nc. */
 rmg_status rmg_hier_coarse_matrix(rmg_hier* hier, int64_t* nc, double* dense, int64_t* ids);
+/* Kernels launched by this library in this process so far (a graph replay counts the
+ * kernels of the graph). Kernels recorded into a graph during capture are not counted. */
+unsigned long long rmg_launch_count(void);
+/* Live timing of the dominant kernel: every V-cycle records CUDA events around one
+ * level-0 smoother stencil launch (the first post-smoothing Chebyshev recurrence step, or the
+ * first post-smoothing Jacobi sweep). rmg_pcg_solve reads them after each of its
+ * per-iteration synchronisations. Returns the accumulated milliseconds and the number of
+ * timed launches since the last reset (reset = 1 clears the totals after reading). */
+rmg_status rmg_hier_probe(rmg_hier* hier, int reset, double* total_ms, long long* count);
 /* Kernel launches queued by one V-cycle (0 when eager mode has not run yet). */
 rmg_status rmg_hier_vcycle_launches(rmg_hier* hier, int* launches);
 

@@ -18,16 +18,22 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from .regions import Layout, incidence, block_diag
+from .regions import Layout, block_diag
 
 
 def share_counts(layout: Layout, A: sp.csr_matrix) -> sp.csr_matrix:
-    """q_ij = number of regions containing both i and j, on the sparsity pattern of A."""
-    M = incidence(layout)
-    Q = (M @ M.T).tocsr()
-    pattern = A.copy()
+    """q_ij = number of regions containing both i and j, on the sparsity pattern of A.
+
+    Every region k contributes a one at each entry (i, j) of A with i and j both in region k:
+    Psi_k (Psi_k^T pattern(A) Psi_k) Psi_k^T, summed over k.
+    """
+    pattern = sp.csr_matrix(A, copy=True)
     pattern.data[:] = 1.0
-    return pattern.multiply(Q).tocsr()
+    Q = None
+    for Pk in layout.Psi_k:
+        inside = (Pk @ (Pk.T @ pattern @ Pk) @ Pk.T).tocsr()
+        Q = inside if Q is None else (Q + inside).tocsr()
+    return Q
 
 
 def split_blocks(layout: Layout, A: sp.csr_matrix):

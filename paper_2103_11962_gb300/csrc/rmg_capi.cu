@@ -137,7 +137,7 @@ rmg_status rmg_operator_from_region_stencils(rmg_layout* lay, int stencil, const
                     (L.dim == 3 && (stencil == 7 || stencil == 27)),
                 RMG_ERR_ARG, "stencil must be 5/9 in 2D and 7/27 in 3D");
     L.kind = stencil;
-    L.coef.alloc((size_t)stencil * L.n_r);
+    L.coef.ensure((size_t)stencil * L.n_r);
     RMG_CUDA(cudaMemcpyAsync(L.coef.get(), coeffs, L.coef.bytes(), cudaMemcpyDeviceToDevice,
                              lay->ctx->c.stream));
     lay->has_operator = true;
@@ -271,6 +271,20 @@ rmg_status rmg_hier_coarse_matrix(rmg_hier* hh, int64_t* nc, double* dense, int6
       RMG_CUDA(cudaMemcpy(ids, h.cu2gid.get(), (size_t)h.nc * sizeof(long long),
                           cudaMemcpyDeviceToHost));
   });
+}
+
+unsigned long long rmg_launch_count(void) { return g_launches; }
+
+rmg_status rmg_hier_probe(rmg_hier* hh, int reset, double* total_ms, long long* count) {
+  if (!hh) return RMG_ERR_ARG;
+  Hier& h = hh->h;
+  if (total_ms) *total_ms = h.probe_ms;
+  if (count) *count = h.probe_count;
+  if (reset) {
+    h.probe_ms = 0.0;
+    h.probe_count = 0;
+  }
+  return RMG_OK;
 }
 
 rmg_status rmg_hier_vcycle_launches(rmg_hier* hh, int* launches) {

@@ -13,6 +13,7 @@ Hier::~Hier() {
   if (graph) cudaGraphDestroy(graph);
   if (graph_stream) cudaStreamDestroy(graph_stream);
   if (pinned) cudaFreeHost(pinned);
+  for (auto e : probe_ev) if (e) cudaEventDestroy(e);
 }
 
 namespace {
@@ -101,9 +102,12 @@ __global__ void k_p_update(int n, const double* __restrict__ z, const Scalars* _
 
 template <class Epi, typename CT, typename VT, typename AT>
 void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
-                    cudaStream_t st, int* launches) {
+                    cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
+                    cudaEvent_t ev1 = nullptr) {
   const Grid G = L.grid();
   const int gb = persistent_grid(c, G.ntiles);
+  // external record nodes when capturing, so the events can be timed after a graph replay
+  if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));
   switch (L.kind) {
     case 5: k_stencil<5, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
     case 7: k_stencil<7, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
@@ -111,6 +115,7 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
     default: k_stencil<27, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
   }
   RMG_LAUNCHED();
+  if (ev1) RMG_CUDA(cudaEventRecordWithFlags(ev1, st, g_capturing ? cudaEventRecordExternal : 0));
   if (launches) ++*launches;
   if (L.ngroups) {
     k_groups<AT><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, st>>>(
@@ -135,6 +140,7 @@ struct Exec {
   Hier& h;
   cudaStream_t st;
   int launches = 0;
+  bool probe = false;        // time the next level-0 phase-A launch with the probe events
   std::vector<VT*> cur, oth;
 
   Exec(Hier& hh, cudaStream_t s) : h(hh), st(s) {}
@@ -148,21 +154,23 @@ struct Exec {
 
   template <class Epi>
   void stencil(int l, const VT* u, Epi epi) {
-    launch_stencil(c(), *h.lv[l], coef(l), u, V(l).y.get(), epi, st, &launches);
+    const bool pr = probe && l == 0 && h.probe_ev[0];
+    launch_stencil(c(), *h.lv[l], coef(l), u, V(l).y.get(), epi, st, &launches,
+                   pr ? h.probe_ev[0] : nullptr, pr ? h.probe_ev[1] : nullptr);
+    if (pr) probe = false;
   }
 
   int elementwise_grid(int n) const { return persistent_grid(c(), (n + 255) / 256); }
 
-  void cheb_step(int l, int k) {   // k >= 1
-    const Level& L = *h.lv[l];
-    (void)L;
+  void cheb_step(int l, int k, bool probe_it = false) {   // k >= 1
+    probe = probe_it;
     EpiCheb<VT> e{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c1[l][k], &sc()->cheb_c2[l][k],
                   V(l).d.get(), oth[l]};
     stencil(l, cur[l], e);
     flip(l);
   }
 
-  void smooth(int l, int nu, bool from_zero) {
+  void smooth(int l, int nu, bool from_zero, bool probe_it = false) {
     const Level& L = *h.lv[l];
     const int n = L.n_r;
     const VT omega = VT(h.o.omega);
@@ -174,6 +182,7 @@ struct Exec {
           RMG_LAUNCHED();
           ++launches;
         } else {
+          probe = probe_it && s == 0;
           stencil(l, cur[l], EpiJacobi<VT>{cur[l], V(l).b.get(), dinv(l), omega, oth[l]});
         }
         flip(l);
@@ -187,11 +196,12 @@ struct Exec {
           RMG_LAUNCHED();
           ++launches;
         } else {
+          probe = probe_it && a == 0 && h.o.cheb_degree == 1;
           stencil(l, cur[l], EpiCheb0<VT>{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c2[l][0],
                                           V(l).d.get(), oth[l]});
         }
         flip(l);
-        for (int k = 1; k < h.o.cheb_degree; ++k) cheb_step(l, k);
+        for (int k = 1; k < h.o.cheb_degree; ++k) cheb_step(l, k, probe_it && a == 0 && k == 1);
       }
     }
   }
@@ -272,7 +282,7 @@ struct Exec {
     coarse(Lv - 1);
     for (int l = Lv - 2; l >= 0; --l) {
       prolong(l);
-      smooth(l, h.o.nu2, false);
+      smooth(l, h.o.nu2, false, l == 0);
     }
   }
 };
@@ -370,7 +380,7 @@ void hier_build(Hier& h) {
   const int Lv = h.levels();
   h.v64.resize(Lv);
   for (int l = 0; l < Lv; ++l) {
-    h.lv[l]->dinv.alloc(h.lv[l]->n_r);
+    h.lv[l]->dinv.ensure(h.lv[l]->n_r);   // level 0 belongs to the layout and may be shared
     h.v64[l].alloc(h.lv[l]->n_r);
   }
   if (h.mixed()) {
@@ -378,9 +388,9 @@ void hier_build(Hier& h) {
     for (int l = 0; l < Lv; ++l) {
       Level& L = *h.lv[l];
       h.v32[l].alloc(L.n_r);
-      L.dinv32.alloc(L.n_r);
-      if (o.precision == RMG_PREC_FP32) L.coef32.alloc((size_t)L.kind * L.n_r);
-      else L.coef16.alloc((size_t)L.kind * L.n_r);
+      L.dinv32.ensure(L.n_r);
+      if (o.precision == RMG_PREC_FP32) L.coef32.ensure((size_t)L.kind * L.n_r);
+      else L.coef16.ensure((size_t)L.kind * L.n_r);
     }
   }
   h.sc.alloc(1);
@@ -389,6 +399,8 @@ void hier_build(Hier& h) {
   h.x.alloc(n0); h.p.alloc(n0); h.q.alloc(n0); h.tmp.alloc(n0);
   h.r.alloc(n0); h.z.alloc(n0); h.zold.alloc(n0);
   RMG_CUDA(cudaHostAlloc(&h.pinned, 64 * sizeof(double), cudaHostAllocDefault));
+  RMG_CUDA(cudaEventCreate(&h.probe_ev[0]));
+  RMG_CUDA(cudaEventCreate(&h.probe_ev[1]));
   // coarsest composite maps
   Level& Lc = *h.lv[Lv - 1];
   DBuf<int> freeflag(Lc.ncomp), pos(Lc.ncomp);
@@ -543,6 +555,14 @@ static void make_low_precision(Hier& h) {
 void hier_numeric(Hier& h) {
   Ctx& c = *h.c;
   const int Lv = h.levels();
+  Level& L0 = *h.lv[0];
+  if (h.gexec) {
+    RMG_REQUIRE(L0.kind == h.kind0 && L0.coef.get() == h.coef0, RMG_ERR_STATE,
+                "the layout's operator changed its stencil since rmg_setup; create a new "
+                "hierarchy");
+  }
+  h.kind0 = L0.kind;
+  h.coef0 = L0.coef.get();
   compute_dinv(h, *h.lv[0]);
   for (int l = 0; l + 1 < Lv; ++l) {
     galerkin(h, *h.lv[l], *h.lv[l + 1]);
@@ -558,9 +578,12 @@ void hier_numeric(Hier& h) {
     RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
     RMG_CUDA(cudaStreamBeginCapture(h.graph_stream, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
+    g_capturing = true;
     try {
       launches = run_cycle(h, h.graph_stream);
+      g_capturing = false;
     } catch (...) {
+      g_capturing = false;
       cudaGraph_t g = nullptr;
       cudaStreamEndCapture(h.graph_stream, &g);
       if (g) cudaGraphDestroy(g);
@@ -573,8 +596,10 @@ void hier_numeric(Hier& h) {
 }
 
 void vcycle(Hier& h) {
+  h.probe_pending = h.levels() > 1 && (h.o.nu2 > 0);
   if (h.gexec) {
     RMG_CUDA(cudaGraphLaunch(h.gexec, h.c->stream));
+    g_launches += (unsigned long long)h.launches;
   } else {
     h.launches = run_cycle(h, h.c->stream);
   }
@@ -604,6 +629,19 @@ void vcycle_apply(Hier& h, const double* r, double* z, int regional) {
   RMG_LAUNCHED();
 }
 
+// Accumulate the timed level-0 smoother launch of the last V-cycle (stream must be idle).
+void probe_collect(Hier& h) {
+  if (!h.probe_pending || !h.probe_ev[0]) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h.probe_ev[0], h.probe_ev[1]) == cudaSuccess) {
+    h.probe_ms += ms;
+    h.probe_count += 1;
+  } else {
+    cudaGetLastError();
+  }
+  h.probe_pending = false;
+}
+
 // ---------------------------------------------------------------------- PCG
 void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, double* history,
                rmg_solve_info* info) {
@@ -629,6 +667,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
     RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
     RMG_CUDA(cudaMemcpyAsync(h.pinned + 1, &sc->bb, sizeof(double), cudaMemcpyDeviceToHost, st));
     RMG_CUDA(cudaStreamSynchronize(st));
+    probe_collect(h);
     *a = h.pinned[0];
     *bb = h.pinned[1];
   };

@@ -36,6 +36,13 @@ struct Hier {
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t graph_stream = nullptr;
   int launches = 0;
+  int kind0 = 0;                             // level-0 stencil and buffer seen by the graph
+  const double* coef0 = nullptr;
+  // probe: CUDA events around one level-0 smoother stencil launch of every V-cycle
+  cudaEvent_t probe_ev[2] = {nullptr, nullptr};
+  bool probe_pending = false;
+  double probe_ms = 0.0;
+  long long probe_count = 0;
   // PCG work vectors (regional, FP64)
   DBuf<double> x, r, z, p, q, zold, tmp;
   double* pinned = nullptr;                  // host-mapped residual read-back
@@ -47,6 +54,7 @@ struct Hier {
 
 void hier_build(Hier& h);          // symbolic: coarse layouts, buffers
 void hier_numeric(Hier& h);        // numeric: diagonals, RAP, lambda, coarse factor, graph
+void probe_collect(Hier& h);       // read the probe events of the last V-cycle
 void vcycle(Hier& h);              // lv[0] rhs in v64[0].b (or v32[0].b) -> result in .u
 void vcycle_apply(Hier& h, const double* r, double* z, int regional);
 void pcg_solve(Hier& h, const double* b, double* x, double rtol, int maxit, double* history,

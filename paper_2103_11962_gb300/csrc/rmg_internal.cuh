@@ -28,7 +28,14 @@ struct Error : std::runtime_error {
       throw ::rmg::Error(e_ == cudaErrorMemoryAllocation ? RMG_ERR_NOMEM : RMG_ERR_CUDA,   \
                          std::string(#x) + ": " + cudaGetErrorString(e_));                 \
   } while (0)
-#define RMG_LAUNCHED() RMG_CUDA(cudaGetLastError())
+// Kernel launches issued by the library (graph replays add the kernels of the graph).
+extern unsigned long long g_launches;
+extern bool g_capturing;
+#define RMG_LAUNCHED()                                  \
+  do {                                                  \
+    RMG_CUDA(cudaGetLastError());                       \
+    if (!::rmg::g_capturing) ++::rmg::g_launches;        \
+  } while (0)
 #define RMG_REQUIRE(cond, st, msg)                     \
   do {                                                 \
     if (!(cond)) throw ::rmg::Error((st), (msg));      \
@@ -64,6 +71,11 @@ struct DBuf {
     release();
     if (count) RMG_CUDA(cudaMalloc(&p, count * sizeof(T)));
     n = count;
+  }
+  // Keep the allocation when it already has `count` elements (pointers captured in a CUDA
+  // graph stay valid); otherwise reallocate.
+  void ensure(size_t count) {
+    if (n != count || (count && !p)) alloc(count);
   }
   void release() {
     if (p) cudaFree(p);

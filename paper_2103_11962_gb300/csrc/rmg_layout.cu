@@ -7,6 +7,9 @@
 
 namespace rmg {
 
+unsigned long long g_launches = 0;
+bool g_capturing = false;
+
 int persistent_grid(const Ctx& c, int work_items, int per_sm) {
   const long cap = (long)c.nsm * per_sm;
   return (int)std::max(1L, std::min<long>(cap, std::max(1, work_items)));
@@ -390,7 +393,7 @@ void split_from_csr(Ctx& c, Level& L, int kind, const int64_t* rowptr, const int
   RMG_REQUIRE((L.dim == 2 && (kind == 5 || kind == 9)) || (L.dim == 3 && (kind == 7 || kind == 27)),
               RMG_ERR_ARG, "stencil must be 5/9 in 2D and 7/27 in 3D");
   L.kind = kind;
-  L.coef.alloc((size_t)kind * L.n_r);
+  L.coef.ensure((size_t)kind * L.n_r);
   const Grid G = L.grid();
   const int gb = persistent_grid(c, G.ntiles);
 #define RMG_SPLIT(K)                                                                        \

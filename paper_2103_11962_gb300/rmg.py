@@ -86,6 +86,9 @@ def lib():
         "rmg_hier_lambda": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "rmg_hier_coarse_matrix": (ctypes.c_int, [P, I64P, P, P]),
         "rmg_hier_vcycle_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+        "rmg_launch_count": (ctypes.c_ulonglong, []),
+        "rmg_hier_probe": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -103,7 +106,12 @@ def exported_symbols():
             "rmg_comp_to_reg", "rmg_reg_to_comp", "rmg_setup", "rmg_setup_numeric",
             "rmg_hier_destroy", "rmg_vcycle_apply", "rmg_pcg_solve", "rmg_hier_level_sizes",
             "rmg_hier_level_export", "rmg_hier_lambda", "rmg_hier_coarse_matrix",
-            "rmg_hier_vcycle_launches"]
+            "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe"]
+
+
+def launch_count() -> int:
+    """Kernels launched by librmg.so so far in this process."""
+    return int(lib().rmg_launch_count())
 
 
 def _ptr(t):
@@ -261,6 +269,13 @@ class Hierarchy:
                                                         dense.ctypes.data_as(P),
                                                         ids.ctypes.data_as(P)))
         return dense, ids
+
+    def probe(self, reset=True):
+        """(total ms, launches) of the timed level-0 smoother kernel since the last reset."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self.ctx.check(lib().rmg_hier_probe(self.h, 1 if reset else 0, ctypes.byref(ms),
+                                            ctypes.byref(n)))
+        return ms.value, n.value
 
     def vcycle_launches(self):
         v = ctypes.c_int()
