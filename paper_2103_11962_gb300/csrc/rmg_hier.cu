@@ -87,7 +87,7 @@ k_cg_update(int n, const double* __restrict__ p, const double* __restrict__ q,
     x[k] = x[k] + a * p[k];
     const double rk = r[k] - a * q[k];
     r[k] = rk;
-    s += (rk * rk) * (1.0 / double(mult[k]));
+    s += (rk * rk) * inv_mult<double>(mult[k]);
   }
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -206,7 +206,9 @@ struct Exec {
     }
   }
 
-  void residual(int l) { stencil(l, cur[l], EpiResid<VT>{V(l).b.get(), V(l).r.get()}); }
+  // r = ([[b]] - Psi^T Psi [[A]] [[u]]) / mult: the regional residual already carrying the
+  // [[Psi Psi^T]]^-1 scaling of the restriction
+  void residual(int l) { stencil(l, cur[l], EpiResidScaled<VT>{V(l).b.get(), V(l).r.get()}); }
 
   void restrict_to(int l) {
     const Level& F = *h.lv[l];
@@ -214,13 +216,11 @@ struct Exec {
     const Grid Gc = C.grid();
     const int gb = persistent_grid(c(), Gc.ntiles);
     if (F.dim == 3)
-      k_restrict<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), F.mult.get(),
-                                              C.mask.get(), C.mult.get(), V(l + 1).b.get(),
-                                              V(l + 1).y.get());
+      k_restrict<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), C.mask.get(),
+                                              C.mult.get(), V(l + 1).b.get(), V(l + 1).y.get());
     else
-      k_restrict<2, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), F.mult.get(),
-                                              C.mask.get(), C.mult.get(), V(l + 1).b.get(),
-                                              V(l + 1).y.get());
+      k_restrict<2, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), C.mask.get(),
+                                              C.mult.get(), V(l + 1).b.get(), V(l + 1).y.get());
     RMG_LAUNCHED();
     ++launches;
     if (C.ngroups) {
@@ -393,6 +393,7 @@ void hier_build(Hier& h) {
       else L.coef16.ensure((size_t)L.kind * L.n_r);
     }
   }
+  if (Lv > 1) h.layout->apbuf.ensure((size_t)(h.lv[0]->dim == 3 ? 27 : 9) * h.lv[0]->n_r);
   h.sc.alloc(1);
   RMG_CUDA(cudaMemsetAsync(h.sc.get(), 0, sizeof(Scalars), c.stream));
   const int n0 = h.lv[0]->n_r;
@@ -446,11 +447,20 @@ static void compute_dinv(Hier& h, Level& L) {
 
 static void galerkin(Hier& h, const Level& F, Level& C) {
   Ctx& c = *h.c;
-  const int gb = persistent_grid(c, (C.n_r + kRapBS - 1) / kRapBS, 16);
-#define RMG_RAP(FK, CK, D)                                                                  \
-  k_rap<FK, CK, D><<<gb, kRapBS, 0, c.stream>>>(C.n_r, C.regions.get(), C.nreg, F.regions.get(), \
-                                                F.coef.get(), F.n_r, F.mask.get(), C.mask.get(),  \
-                                                C.mult.get(), C.coef.get())
+  double* ap = h.layout->apbuf.get();
+  const Grid Gf = F.grid(), Gc = C.grid();
+  const int gf = persistent_grid(c, Gf.ntiles), gc = persistent_grid(c, Gc.ntiles);
+#define RMG_RAP(FK, CK, D)                                                                    \
+  {                                                                                           \
+    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
+    RMG_CUDA(cudaFuncSetAttribute(k_ap<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                  smem));                                                     \
+    k_ap<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), F.mask.get(), \
+                                               C.mask.get(), ap);                             \
+  }                                                                                           \
+  RMG_LAUNCHED();                                                                             \
+  k_rtap<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, C.mask.get(),     \
+                                            C.mult.get(), C.coef.get())
   switch (F.kind) {
     case 5: RMG_RAP(5, 9, 2); break;
     case 9: RMG_RAP(9, 9, 2); break;
@@ -528,7 +538,7 @@ static void coarse_factor(Hier& h) {
   c.check_device_error("rmg_setup (coarse factorisation)");
   // the assembled matrix is kept in Ainv's slot until the inverse overwrites it
   DBuf<double> Linv((size_t)nc * nc);
-  k_trinv<<<std::max(1, (nc + 63) / 64), 64, 0, st>>>(h.Mfac.get(), nc, Linv.get());
+  k_trinv<<<std::max(1, (nc + 7) / 8), 256, 0, st>>>(h.Mfac.get(), nc, Linv.get());
   RMG_LAUNCHED();
   const int t = (nc + 15) / 16;
   k_xtx<<<dim3(t, t), dim3(16, 16), 0, st>>>(Linv.get(), nc, h.Ainv.get());

@@ -188,7 +188,7 @@ struct Scalars {
   double lam[16];          // power-method estimate per level
   double cheb_c1[16][8];   // Chebyshev d <- c1 d + c2 D^-1 r, per level and step
   double cheb_c2[16][8];
-  double pw_norm;          // power method scratch
+  double pw_norm, pw_inv;  // power method scratch (norm and its reciprocal)
   double pw_num, pw_den;
   double rz, pq, alpha, beta, rr, bb, rz_new;
 };
@@ -223,4 +223,5 @@ struct rmg_layout {
   bool has_operator = false;
   rmg::DBuf<double> ybuf;         // interface partials for rmg_regional_apply
   rmg::DBuf<double> tmp;          // composite temp
+  rmg::DBuf<double> apbuf;        // Galerkin-product scratch (rows of [[A]][[P]]), all hierarchies
 };

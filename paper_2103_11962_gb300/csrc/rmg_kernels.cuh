@@ -86,7 +86,7 @@ k_stencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
     int i, j, l;
     decode(li, R, i, j, l);
     const AT au = stencil_row<KIND, CT, VT, AT>(coef, u, n, G.n_r, i, j, l, R);
-    if (mult[n] > 1) y[n] = au; else epi(n, au);
+    if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
   RMG_END_FOR_NODES
 }
 
@@ -99,33 +99,54 @@ k_groups(int ngroups, const int* __restrict__ gptr, const int* __restrict__ gslo
     const int a = gptr[g], e = gptr[g + 1];
     AT s = AT(0);
     for (int k = a; k < e; ++k) s += y[gslot[k]];
-    for (int k = a; k < e; ++k) epi(gslot[k], s);
+    for (int k = a; k < e; ++k) epi(gslot[k], s, e - a);
   }
 }
 
 // ------------------------------------------------------------------ epilogues
+// An epilogue receives the node, the composite row result (A u)_n and the multiplicity m of
+// the node (1 in phase A, the group size in phase B).
+
+// 1/m without a division for the multiplicities of box tilings (1, 2, 4, 8).
+template <typename T>
+__device__ __forceinline__ T inv_mult(int m) {
+  switch (m) {
+    case 1: return T(1);
+    case 2: return T(0.5);
+    case 4: return T(0.25);
+    case 8: return T(0.125);
+    default: return T(1) / T(m);
+  }
+}
+
 template <typename T>
 struct EpiStore {                 // out = A u
   T* out;
-  __device__ void operator()(int n, T au) const { out[n] = au; }
+  __device__ void operator()(int n, T au, int) const { out[n] = au; }
 };
 
 template <typename T>
 struct EpiScaled {                // out = D~^-1 A u (power method)
   const T* dinv; T* out;
-  __device__ void operator()(int n, T au) const { out[n] = dinv[n] * au; }
+  __device__ void operator()(int n, T au, int) const { out[n] = dinv[n] * au; }
 };
 
 template <typename T>
 struct EpiResid {                 // r = b - A u
   const T* b; T* r;
-  __device__ void operator()(int n, T au) const { r[n] = b[n] - au; }
+  __device__ void operator()(int n, T au, int) const { r[n] = b[n] - au; }
+};
+
+template <typename T>
+struct EpiResidScaled {           // r = (b - A u) / mult: the [[Psi Psi^T]]^-1 of restriction
+  const T* b; T* r;
+  __device__ void operator()(int n, T au, int m) const { r[n] = (b[n] - au) * inv_mult<T>(m); }
 };
 
 template <typename T>
 struct EpiJacobi {                // u_out = u + omega D~^-1 (b - A u)
   const T* u; const T* b; const T* dinv; T omega; T* uo;
-  __device__ void operator()(int n, T au) const {
+  __device__ void operator()(int n, T au, int) const {
     const T r = b[n] - au;
     uo[n] = fma(omega * dinv[n], r, u[n]);
   }
@@ -134,7 +155,7 @@ struct EpiJacobi {                // u_out = u + omega D~^-1 (b - A u)
 template <typename T>
 struct EpiCheb0 {                 // first Chebyshev step: d = D~^-1 r / theta, u_out = u + d
   const T* u; const T* b; const T* dinv; const double* c2; T* d; T* uo;
-  __device__ void operator()(int n, T au) const {
+  __device__ void operator()(int n, T au, int) const {
     const T r = b[n] - au;
     const T dn = (dinv[n] * r) * T(*c2);
     d[n] = dn;
@@ -145,7 +166,7 @@ struct EpiCheb0 {                 // first Chebyshev step: d = D~^-1 r / theta, 
 template <typename T>
 struct EpiCheb {                  // d = c1 d + c2 D~^-1 r, u_out = u + d
   const T* u; const T* b; const T* dinv; const double* c1; const double* c2; T* d; T* uo;
-  __device__ void operator()(int n, T au) const {
+  __device__ void operator()(int n, T au, int) const {
     const T r = b[n] - au;
     const T dn = T(*c1) * d[n] + (T(*c2) * dinv[n]) * r;
     d[n] = dn;
@@ -174,94 +195,101 @@ __global__ void k_cheb0_zero(int n, const T* __restrict__ b, const T* __restrict
 }
 
 // ------------------------------------------------------------------ transfers (Sec. 3.3)
-// 1D linear 3:1 weight of the coarse node at fine offset a in [-2, 2] from it. The right
-// weight of a fine node with remainder rem is rem/3 and the left one 1 - rem/3.
-__device__ __forceinline__ double w1d(int a) {
-  switch (a) {
-    case -2: return 1.0 / 3.0;          // rem 1, coarse node on the right
-    case -1: return 2.0 / 3.0;          // rem 2, coarse node on the right
-    case 0: return 1.0;
-    case 1: return 1.0 - 1.0 / 3.0;     // rem 1, coarse node on the left
-    default: return 1.0 - 2.0 / 3.0;    // rem 2, coarse node on the left
-  }
+// 1D linear 3:1 interpolation: a fine node with remainder rem = i mod 3 takes weight
+// 1 - rem/3 from coarse node i/3 and rem/3 from coarse node i/3 + 1. Seen from a coarse node,
+// the fine node at offset a in [-2, 2] carries w1d(a). All weights are compile-time constants.
+__host__ __device__ constexpr double w1d(int a) {
+  return a == -2 ? 1.0 / 3.0 : a == -1 ? 2.0 / 3.0 : a == 0 ? 1.0
+       : a == 1 ? 1.0 - 1.0 / 3.0 : 1.0 - 2.0 / 3.0;
+}
+// Weight of the left (side 0) or right (side 1) coarse node of a fine node with remainder rem.
+__host__ __device__ constexpr double wrem(int rem, int side) {
+  return rem == 0 ? (side == 0 ? 1.0 : 0.0)
+       : side == 1 ? rem / 3.0 : 1.0 - rem / 3.0;
 }
 
-// Region-local restriction w_loc = [[R]] (r / mult) for every coarse node of the level,
-// zero at masked coarse nodes (their column of P is zero). Shared coarse nodes store into
-// y for the coarse interface sum (Psibar^T Psibar).
+// Region-local restriction w = [[R]] rs for every coarse node, rs = r / mult being the
+// residual already scaled by [[Psi Psi^T]]^-1. Zero at masked coarse nodes (their column of
+// P is zero). Shared coarse nodes store into yc for the coarse interface sum.
+template <int DIM, bool CHECK, typename VT>
+__device__ __forceinline__ VT restrict_sum(const VT* __restrict__ rs, const RegionDev& F,
+                                           int I, int J, int L) {
+  VT acc = VT(0);
+  constexpr int ZL = DIM == 3 ? -2 : 0, ZH = DIM == 3 ? 2 : 0;
+#pragma unroll
+  for (int c = ZL; c <= ZH; ++c) {
+    const int fz = DIM == 3 ? 3 * L + c : 0;
+    if (CHECK && (fz < 0 || fz >= F.nz)) continue;
+#pragma unroll
+    for (int b = -2; b <= 2; ++b) {
+      const int fy = 3 * J + b;
+      if (CHECK && (fy < 0 || fy >= F.ny)) continue;
+      const int row = F.off + F.nx * (fy + F.ny * fz);
+#pragma unroll
+      for (int a = -2; a <= 2; ++a) {
+        const int fx = 3 * I + a;
+        if (CHECK && (fx < 0 || fx >= F.nx)) continue;
+        constexpr double dummy = 0.0;
+        (void)dummy;
+        const VT wgt = VT((DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a)));
+        acc = fma(wgt, rs[row + fx], acc);
+      }
+    }
+  }
+  return acc;
+}
+
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kTile)
-k_restrict(Grid Gc, const RegionDev* __restrict__ fregions, const VT* __restrict__ r,
-           const uint8_t* __restrict__ fmult, const uint8_t* __restrict__ cmask,
-           const uint8_t* __restrict__ cmult, VT* __restrict__ w, VT* __restrict__ yc) {
+k_restrict(Grid Gc, const RegionDev* __restrict__ fregions, const VT* __restrict__ rs,
+           const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult,
+           VT* __restrict__ w, VT* __restrict__ yc) {
   RMG_FOR_NODES(Gc)
     int I, J, L;
     decode(li, R, I, J, L);
     VT acc = VT(0);
     if (!cmask[n]) {
       const RegionDev F = fregions[tile_.region];
-      const int zlo = DIM == 3 ? -2 : 0, zhi = DIM == 3 ? 2 : 0;
-      for (int c = zlo; c <= zhi; ++c) {
-        const int fz = 3 * L + c;
-        if (fz < 0 || fz >= F.nz) continue;
-        const double wz = DIM == 3 ? w1d(c) : 1.0;
-        for (int b = -2; b <= 2; ++b) {
-          const int fy = 3 * J + b;
-          if (fy < 0 || fy >= F.ny) continue;
-          const double wy = w1d(b);
-          for (int a = -2; a <= 2; ++a) {
-            const int fx = 3 * I + a;
-            if (fx < 0 || fx >= F.nx) continue;
-            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-            const VT wgt = VT(wz * (wy * w1d(a)));
-            const VT sc = r[f] * (VT(1) / VT(fmult[f]));
-            acc = fma(wgt, sc, acc);
-          }
-        }
-      }
+      const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
+                         (DIM == 2 || (L > 0 && L < R.nz - 1));
+      acc = inner ? restrict_sum<DIM, false, VT>(rs, F, I, J, L)
+                  : restrict_sum<DIM, true, VT>(rs, F, I, J, L);
     }
     if (cmult[n] > 1) yc[n] = acc; else w[n] = acc;
   RMG_END_FOR_NODES
 }
 
 // Region-local interpolation and correction u += [[P]] ubar (no inter-region exchange).
+// The products wz (wy wx) of the up to 8 weights of a fine node come from a shared table
+// indexed by the three remainders.
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kTile)
 k_prolong(Grid Gf, const RegionDev* __restrict__ cregions, const uint8_t* __restrict__ fmask,
           const VT* __restrict__ ubar, VT* __restrict__ u) {
+  __shared__ VT tab[27 * 8];
+  for (int e = threadIdx.x; e < 27 * 8; e += blockDim.x) {
+    const int r = e >> 3, combo = e & 7;
+    const int rx = r % 3, ry = (r / 3) % 3, rz = r / 9;
+    const int sa = combo & 1, sb = (combo >> 1) & 1, sc = combo >> 2;
+    tab[e] = VT(wrem(rz, sc) * (wrem(ry, sb) * wrem(rx, sa)));
+  }
+  __syncthreads();
   RMG_FOR_NODES(Gf)
     if (fmask[n]) continue;
     int i, j, l;
     decode(li, R, i, j, l);
     const RegionDev C = cregions[tile_.region];
-    int cx[2], cy[2], cz[2];
-    double wx[2], wy[2], wz[2];
-    int nxs, nys, nzs;
-    {
-      const int c0 = i / 3, rem = i - 3 * c0;
-      cx[0] = c0; wx[0] = rem ? 1.0 - rem / 3.0 : 1.0; cx[1] = c0 + 1; wx[1] = rem / 3.0;
-      nxs = rem ? 2 : 1;
-    }
-    {
-      const int c0 = j / 3, rem = j - 3 * c0;
-      cy[0] = c0; wy[0] = rem ? 1.0 - rem / 3.0 : 1.0; cy[1] = c0 + 1; wy[1] = rem / 3.0;
-      nys = rem ? 2 : 1;
-    }
-    if (DIM == 3) {
-      const int c0 = l / 3, rem = l - 3 * c0;
-      cz[0] = c0; wz[0] = rem ? 1.0 - rem / 3.0 : 1.0; cz[1] = c0 + 1; wz[1] = rem / 3.0;
-      nzs = rem ? 2 : 1;
-    } else {
-      cz[0] = 0; wz[0] = 1.0; nzs = 1;
-    }
+    const int cx = i / 3, rx = i - 3 * cx;
+    const int cy = j / 3, ry = j - 3 * cy;
+    const int cz = DIM == 3 ? l / 3 : 0, rz = DIM == 3 ? l - 3 * cz : 0;
+    const int nxs = rx ? 2 : 1, nys = ry ? 2 : 1, nzs = rz ? 2 : 1;
+    const VT* t = tab + 8 * (rx + 3 * ry + 9 * rz);
+    const int base = C.off + cx + C.nx * (cy + C.ny * cz);
     VT acc = VT(0);
     for (int c = 0; c < nzs; ++c)
       for (int b = 0; b < nys; ++b)
-        for (int a = 0; a < nxs; ++a) {
-          const int k = C.off + cx[a] + C.nx * (cy[b] + C.ny * cz[c]);
-          const VT wgt = VT(wz[c] * (wy[b] * wx[a]));
-          acc = fma(wgt, ubar[k], acc);
-        }
+        for (int a = 0; a < nxs; ++a)
+          acc = fma(t[a + 2 * b + 4 * c], ubar[base + a + C.nx * (b + C.ny * c)], acc);
     u[n] = u[n] + acc;
   RMG_END_FOR_NODES
 }
@@ -294,7 +322,7 @@ k_dot(int n, const XT* __restrict__ x, const YT* __restrict__ y, const uint8_t* 
       double* __restrict__ partials) {
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    s += (double(x[k]) * double(y[k])) * (1.0 / double(mult[k]));
+    s += (double(x[k]) * double(y[k])) * inv_mult<double>(mult[k]);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }

@@ -58,95 +58,133 @@ __global__ void k_diag_local(int n_r, const double* __restrict__ coef,
 
 struct EpiRecip {
   double* dinv;
-  __device__ void operator()(int n, double s) const { dinv[n] = 1.0 / s; }
+  __device__ void operator()(int n, double s, int) const { dinv[n] = 1.0 / s; }
 };
 
 // ------------------------------------------------------------------ Galerkin product
-// [[Abar]] = [[R]] [[A]] [[P]] for one coarse node per thread (eq. RegionalGalerkinProduct),
-// evaluated region-locally from the definition: sum over the fine nodes f in the support of
-// the coarse basis function, their stencil neighbours f', and the coarse nodes C' that f'
-// interpolates from. Masked fine nodes have zero P rows, masked coarse nodes zero P
-// columns; a masked coarse row becomes 1/mult on the diagonal.
-constexpr int kRapBS = 128;
+// [[Abar]] = [[R]] [[A]] [[P]] (eq. RegionalGalerkinProduct), region by region, in two steps
+// following the product order R (A P):
+//  1. k_ap: for every fine node f, row f of [[A]] [[P]], i.e. sum_s A_s(f) P(f + d_s, C') for
+//     the (at most 3 per axis) coarse nodes C' near f, stored relative to the coarse node
+//     (x - 1) div 3 on each axis: ap[o][f], o = ox + 3 oy + 9 oz.
+//  2. k_rtap: for every coarse node C, sum over the fine nodes f = 3C + (a, b, c) of its
+//     support of P(f, C) ap[.][f]; the weights P(f, C) are compile-time constants.
+// Masked fine nodes have zero rows of P, masked coarse nodes zero columns; a masked coarse
+// row becomes 1/mult on the diagonal so that the composite sum is the identity row.
+__device__ __forceinline__ int floor_div3m1(int x) { return (x + 2) / 3 - 1; }   // (x-1) div 3, x >= 0
 
-template <int FK, int CK, int DIM>
-__global__ void __launch_bounds__(kRapBS)
-k_rap(int cn_r, const RegionDev* __restrict__ cregs, int nreg, const RegionDev* __restrict__ fregs,
-      const double* __restrict__ fcoef, int fn_r, const uint8_t* __restrict__ fmask,
-      const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult,
-      double* __restrict__ ccoef) {
+template <int FK, int DIM>
+__global__ void __launch_bounds__(kTile)
+k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fcoef,
+     const uint8_t* __restrict__ fmask, const uint8_t* __restrict__ cmask,
+     double* __restrict__ ap) {
   using FS = Sten<FK>;
-  using CS = Sten<CK>;
-  __shared__ double acc[CS::S][kRapBS];
+  constexpr int NO = DIM == 3 ? 27 : 9;
+  __shared__ double tab[27 * 8];
+  extern __shared__ double ap_acc[];                 // NO x kTile accumulators (dynamic)
+  double (*acc)[kTile] = reinterpret_cast<double (*)[kTile]>(ap_acc);
+  for (int e = threadIdx.x; e < 27 * 8; e += blockDim.x) {
+    const int r = e >> 3, combo = e & 7;
+    tab[e] = wrem(r / 9, combo >> 2) * (wrem((r / 3) % 3, (combo >> 1) & 1) * wrem(r % 3, combo & 1));
+  }
+  __syncthreads();
   const int tid = threadIdx.x;
-  for (int base = blockIdx.x * kRapBS; base < cn_r; base += gridDim.x * kRapBS) {
-    const int C = base + tid;
-    const bool live = C < cn_r;
+  RMG_FOR_NODES(Gf)
 #pragma unroll
-    for (int s = 0; s < CS::S; ++s) acc[s][tid] = 0.0;
-    if (live) {
-      const int k = region_of(cregs, nreg, C);
-      const RegionDev Cr = cregs[k];
-      const RegionDev F = fregs[k];
-      int I, J, L;
-      decode(C - Cr.off, Cr, I, J, L);
-      if (cmask[C]) {
-        acc[CS::CENTER][tid] = 1.0 / (double)cmult[C];
-      } else {
-        const int zlo = DIM == 3 ? -2 : 0, zhi = DIM == 3 ? 2 : 0;
-        for (int c = zlo; c <= zhi; ++c) {
-          const int fz = 3 * L + c;
-          if (fz < 0 || fz >= F.nz) continue;
-          const double wz = DIM == 3 ? w1d(c) : 1.0;
-          for (int b = -2; b <= 2; ++b) {
-            const int fy = 3 * J + b;
-            if (fy < 0 || fy >= F.ny) continue;
-            const double wy = w1d(b);
-            for (int a = -2; a <= 2; ++a) {
-              const int fx = 3 * I + a;
-              if (fx < 0 || fx >= F.nx) continue;
-              const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-              if (fmask[f]) continue;
-              const double wf = wz * (wy * w1d(a));
+    for (int o = 0; o < NO; ++o) acc[o][tid] = 0.0;
+    if (!fmask[n]) {
+      int x, y, z;
+      decode(li, R, x, y, z);
+      const RegionDev C = cregs[tile_.region];
+      const int cx0 = floor_div3m1(x), cy0 = floor_div3m1(y), cz0 = DIM == 3 ? floor_div3m1(z) : 0;
 #pragma unroll
-              for (int s = 0; s < FS::S; ++s) {
-                const int gx = fx + FS::dx(s), gy = fy + FS::dy(s), gz = fz + FS::dz(s);
-                if (gx < 0 || gx >= F.nx || gy < 0 || gy >= F.ny || gz < 0 || gz >= F.nz) continue;
-                const double v = fcoef[(size_t)s * fn_r + f];
-                if (v == 0.0) continue;
-                const int f2 = F.off + gx + F.nx * (gy + F.ny * gz);
-                if (fmask[f2]) continue;
-                const double wv = wf * v;
-                // coarse nodes that f2 interpolates from
-                const int x0 = gx / 3, rx = gx - 3 * x0;
-                const int y0 = gy / 3, ry = gy - 3 * y0;
-                const int z0 = gz / 3, rz = gz - 3 * z0;
-                const int nxs = rx ? 2 : 1, nys = ry ? 2 : 1, nzs = (DIM == 3 && rz) ? 2 : 1;
-                for (int zc = 0; zc < nzs; ++zc) {
-                  const double wcz = DIM == 3 ? (rz ? (zc ? rz / 3.0 : 1.0 - rz / 3.0) : 1.0) : 1.0;
-                  const int Z = z0 + zc;
-                  for (int yc = 0; yc < nys; ++yc) {
-                    const double wcy = ry ? (yc ? ry / 3.0 : 1.0 - ry / 3.0) : 1.0;
-                    const int Y = y0 + yc;
-                    for (int xc = 0; xc < nxs; ++xc) {
-                      const double wcx = rx ? (xc ? rx / 3.0 : 1.0 - rx / 3.0) : 1.0;
-                      const int X = x0 + xc;
-                      const int Cn = Cr.off + X + Cr.nx * (Y + Cr.ny * Z);
-                      if (cmask[Cn]) continue;
-                      const int slot = sten_slot<CK>(X - I, Y - J, DIM == 3 ? Z - L : 0);
-                      acc[slot][tid] += wv * (wcz * (wcy * wcx));
-                    }
-                  }
-                }
-              }
+      for (int s = 0; s < FS::S; ++s) {
+        const int gx = x + FS::dx(s), gy = y + FS::dy(s), gz = z + FS::dz(s);
+        if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
+        const double v = fcoef[(size_t)s * Gf.n_r + n];
+        if (v == 0.0) continue;
+        if (fmask[R.off + gx + R.nx * (gy + R.ny * gz)]) continue;
+        const int x0 = gx / 3, rx = gx - 3 * x0;
+        const int y0 = gy / 3, ry = gy - 3 * y0;
+        const int z0 = DIM == 3 ? gz / 3 : 0, rz = DIM == 3 ? gz - 3 * z0 : 0;
+        const double* t = tab + 8 * (rx + 3 * ry + 9 * rz);
+        for (int c = 0; c < (rz ? 2 : 1); ++c)
+          for (int b = 0; b < (ry ? 2 : 1); ++b)
+            for (int a = 0; a < (rx ? 2 : 1); ++a) {
+              const int X = x0 + a, Y = y0 + b, Z = z0 + c;
+              if (cmask[C.off + X + C.nx * (Y + C.ny * Z)]) continue;
+              const int o = (X - cx0) + 3 * (Y - cy0) + 9 * (Z - cz0);
+              acc[o][tid] = fma(v, t[a + 2 * b + 4 * c], acc[o][tid]);
             }
-          }
-        }
       }
+    }
 #pragma unroll
-      for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * cn_r + C] = acc[s][tid];
+    for (int o = 0; o < NO; ++o) ap[(size_t)o * Gf.n_r + n] = acc[o][tid];
+  RMG_END_FOR_NODES
+}
+
+template <int DIM, bool CHECK>
+__device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r,
+                                         const RegionDev& F, int I, int J, int L,
+                                         double (&acc)[27]) {
+  constexpr int ZL = DIM == 3 ? -2 : 0, ZH = DIM == 3 ? 2 : 0;
+#pragma unroll
+  for (int c = ZL; c <= ZH; ++c) {
+    const int fz = DIM == 3 ? 3 * L + c : 0;
+    if (CHECK && (fz < 0 || fz >= F.nz)) continue;
+#pragma unroll
+    for (int b = -2; b <= 2; ++b) {
+      const int fy = 3 * J + b;
+      if (CHECK && (fy < 0 || fy >= F.ny)) continue;
+#pragma unroll
+      for (int a = -2; a <= 2; ++a) {
+        const int fx = 3 * I + a;
+        if (CHECK && (fx < 0 || fx >= F.nx)) continue;
+        const int f = F.off + fx + F.nx * (fy + F.ny * fz);
+        const double wf = (DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a));
+        // ap of node f is stored relative to the coarse node (f - 1) div 3 on each axis,
+        // which is C - 1 for offsets a <= 0 and C for a >= 1
+        const int bx = a <= 0 ? 1 : 0, by = b <= 0 ? 1 : 0, bz = DIM == 3 ? (c <= 0 ? 1 : 0) : 0;
+#pragma unroll
+        for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
+#pragma unroll
+          for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+              const int ix = ox + bx, iy = oy + by, iz = oz + bz;
+              if (ix < 0 || ix > 2 || iy < 0 || iy > 2 || iz < 0 || iz > 2) continue;
+              const int slot = (ox + 1) + 3 * (oy + 1) + (DIM == 3 ? 9 * (oz + 1) : 0);
+              acc[slot] = fma(wf, ap[(size_t)(ix + 3 * iy + 9 * iz) * fn_r + f], acc[slot]);
+            }
+      }
     }
   }
+}
+
+template <int CK, int DIM>
+__global__ void __launch_bounds__(kTile)
+k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
+       const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult,
+       double* __restrict__ ccoef) {
+  using CS = Sten<CK>;
+  RMG_FOR_NODES(Gc)
+    double acc[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+    if (cmask[n]) {
+      acc[DIM == 3 ? 13 : 4] = 1.0 / (double)cmult[n];
+    } else {
+      int I, J, L;
+      decode(li, R, I, J, L);
+      const RegionDev F = fregs[tile_.region];
+      const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
+                         (DIM == 2 || (L > 0 && L < R.nz - 1));
+      if (inner) rtap_sum<DIM, false>(ap, fn_r, F, I, J, L, acc);
+      else rtap_sum<DIM, true>(ap, fn_r, F, I, J, L, acc);
+    }
+#pragma unroll
+    for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
+  RMG_END_FOR_NODES
 }
 
 // ------------------------------------------------------------------ power method (Sec. 3.4)
@@ -167,18 +205,28 @@ __global__ void k_power_init(int n_r, const int* __restrict__ gid, const uint8_t
 }
 
 // out = sum of partials, then an operation on the scalar block.
+// FIN_SQRT stores sqrt(sum) in dst[0] and its reciprocal in dst[1].
 enum FinOp : int { FIN_SQRT = 0, FIN_STORE = 1 };
 __global__ void k_finalize(const double* __restrict__ partials, int np, double* __restrict__ dst,
                            int op) {
   const double s = sum_partials(partials, np);
-  if (threadIdx.x == 0) *dst = (op == FIN_SQRT) ? sqrt(s) : s;
+  if (threadIdx.x == 0) {
+    if (op == FIN_SQRT) {
+      const double r = sqrt(s);
+      dst[0] = r;
+      dst[1] = 1.0 / r;
+    } else {
+      dst[0] = s;
+    }
+  }
 }
 
+// out = x / ||x|| as a product with the stored reciprocal norm.
 __global__ void k_scale_div(int n, const double* __restrict__ x, const double* __restrict__ nrm,
                             double* __restrict__ out) {
-  const double d = *nrm;
+  const double d = nrm[1];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    out[k] = x[k] / d;
+    out[k] = x[k] * d;
 }
 
 // lambda = num / den, then the Chebyshev coefficient table of Algorithm 2 for this level.
@@ -327,34 +375,42 @@ __global__ void k_chol_update(double* M, int n, int k0, int k1) {
   }
 }
 
-// X = L^-1 (lower), one thread per column, X row-major (coalesced across columns).
-__global__ void k_trinv(const double* __restrict__ L, int n, double* __restrict__ X) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    for (int i = 0; i < j; ++i) X[(size_t)i * n + j] = 0.0;
+// Xc = (L^-1)^T stored row by row: row j of Xc is column j of L^-1. One warp per column:
+// forward substitution, the dot product over earlier rows split across the lanes.
+__global__ void k_trinv(const double* __restrict__ L, int n, double* __restrict__ Xc) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < n; j += nwarps) {
+    double* x = Xc + (size_t)j * n;
+    for (int i = lane; i < j; i += 32) x[i] = 0.0;
     for (int i = j; i < n; ++i) {
-      double acc = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) acc -= L[(size_t)i * n + k] * X[(size_t)k * n + j];
-      X[(size_t)i * n + j] = acc / L[(size_t)i * n + i];
+      const double* Li = L + (size_t)i * n;
+      double s = 0.0;
+      for (int k = j + lane; k < i; k += 32) s = fma(Li[k], x[k], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
+      __syncwarp();
     }
   }
 }
 
-// Ainv = X^T X (X = L^-1 lower triangular).
-__global__ void k_xtx(const double* __restrict__ X, int n, double* __restrict__ Ainv) {
+// Ainv = L^-T L^-1: Ainv[i][j] = sum_k Xc[i][k] Xc[j][k].
+__global__ void k_xtx(const double* __restrict__ Xc, int n, double* __restrict__ Ainv) {
   __shared__ double A[16][17], B[16][17];
-  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int tx = threadIdx.x, ty = threadIdx.y;
   double s = 0.0;
-  const int kstart = (min(blockIdx.y, blockIdx.x) * 16);
-  for (int k0 = kstart; k0 < n; k0 += 16) {
-    const int kr = k0 + threadIdx.y;
-    A[threadIdx.y][threadIdx.x] =
-        (kr < n && blockIdx.y * 16 + threadIdx.x < n) ? X[(size_t)kr * n + blockIdx.y * 16 + threadIdx.x] : 0.0;
-    B[threadIdx.y][threadIdx.x] = (kr < n && j < n) ? X[(size_t)kr * n + j] : 0.0;
+  for (int k0 = max(i0, j0) / 16 * 16; k0 < n; k0 += 16) {
+    A[ty][tx] = (i0 + ty < n && k0 + tx < n) ? Xc[(size_t)(i0 + ty) * n + k0 + tx] : 0.0;
+    B[ty][tx] = (j0 + ty < n && k0 + tx < n) ? Xc[(size_t)(j0 + ty) * n + k0 + tx] : 0.0;
     __syncthreads();
-    for (int k = 0; k < 16; ++k) s += A[k][threadIdx.y] * B[k][threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s = fma(A[ty][k], B[tx][k], s);
     __syncthreads();
   }
-  if (i < n && j < n) Ainv[(size_t)i * n + j] = s;
+  if (i0 + ty < n && j0 + tx < n) Ainv[(size_t)(i0 + ty) * n + j0 + tx] = s;
 }
 
 }  // namespace rmg
