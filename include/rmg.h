@@ -185,6 +185,38 @@ rmg_status rmg_vcycle_apply(rmg_hier* hier, const double* r, double* z, int layo
 rmg_status rmg_pcg_solve(rmg_hier* hier, const double* b, double* x, double rtol, int maxit,
                          double* history, rmg_solve_info* info);
 
+/*
+ * Regional operator apply that allocates no device memory: y = Psi^T Psi [[A]] u, the same
+ * result as rmg_regional_apply, for callers that cannot call cudaMalloc at that point
+ * (applications whose own pool allocator owns all device memory, loops that cannot afford
+ * the device-wide synchronisation an allocation or a free can cause). The
+ * paper has no counterpart: it is a deployment variant of the interface summation.
+ * No handle is needed; every argument is a plain array:
+ *   dim, nregions, region_dims (host int32[3*m]), region_gids (device int64[n_r]),
+ *   n_composite  as for rmg_layout_create (no Dirichlet mask: masked rows are already
+ *                identity rows of the split operator)
+ *   stencil, coeffs  already-split region stencils, device double[stencil * n_r], slot-major
+ *                (the layout of rmg_operator_from_region_stencils / rmg_hier_level_export)
+ *   u, y         device regional vectors (u consistent); y is consistent on return
+ *   cuda_stream  stream for the work (NULL = legacy default stream)
+ *   msg, msg_len optional caller buffer that receives the error text
+ * Scratch: one file-scope device array of about 32 MiB held by every GPU that loads the
+ * library until the process exits, with room for at most 4096 regions and 4,194,304
+ * composite nodes; larger inputs fail with RMG_ERR_ARG before any work is queued. Each call
+ * rewrites the region table and zeroes the accumulator it keeps there; calls that overlap
+ * on the GPU (other streams or host threads) share the array and race. The first call on a
+ * device takes the device address of the array (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. The summation order over the
+ * copies of an interface node is not fixed (atomic adds), so results can differ from
+ * rmg_regional_apply in the last bits. Regional nodes whose gid is outside
+ * [0, n_composite) receive NaN. Returns once the work is queued.
+ */
+rmg_status rmg_regional_apply_static(int dim, int nregions, const int32_t* region_dims,
+                                     int stencil, const double* coeffs,
+                                     const int64_t* region_gids, int64_t n_composite,
+                                     const double* u, double* y, void* cuda_stream, char* msg,
+                                     int msg_len);
+
 /* ---- introspection (tests and benchmarks) ------------------------------------------- */
 /* Levels, and per level: regions, regional nodes, composite id space, stencil points. */
 rmg_status rmg_hier_level_sizes(rmg_hier* hier, int level, int64_t* n_regional,

@@ -87,6 +87,9 @@ def lib():
         "rmg_hier_coarse_matrix": (ctypes.c_int, [P, I64P, P, P]),
         "rmg_hier_vcycle_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_launch_count": (ctypes.c_ulonglong, []),
+        "rmg_regional_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
+                                                     P, P, ctypes.c_int64, P, P, P,
+                                                     ctypes.c_char_p, ctypes.c_int]),
         "rmg_hier_probe": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_longlong)]),
     }
@@ -106,7 +109,24 @@ def exported_symbols():
             "rmg_comp_to_reg", "rmg_reg_to_comp", "rmg_setup", "rmg_setup_numeric",
             "rmg_hier_destroy", "rmg_vcycle_apply", "rmg_pcg_solve", "rmg_hier_level_sizes",
             "rmg_hier_level_export", "rmg_hier_lambda", "rmg_hier_coarse_matrix",
-            "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe"]
+            "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
+            "rmg_regional_apply_static"]
+
+
+def regional_apply_static(dim, region_dims, stencil, coeffs, region_gids, n_composite, u, y,
+                          stream=None):
+    """y = Psi^T Psi [[A]] u through the entry point that allocates no device memory.
+
+    For callers that cannot allocate device memory when they apply the operator; the
+    scratch lives in a fixed device array inside librmg.so (see include/rmg.h)."""
+    rd = np.ascontiguousarray(np.asarray(region_dims, dtype=np.int32).reshape(-1))
+    buf = ctypes.create_string_buffer(512)
+    st = lib().rmg_regional_apply_static(int(dim), rd.size // 3, rd.ctypes.data_as(P),
+                                         int(stencil), _ptr(coeffs), _ptr(region_gids),
+                                         int(n_composite), _ptr(u), _ptr(y),
+                                         ctypes.c_void_p(stream or 0), buf, 512)
+    if st != RMG_OK:
+        raise RmgError(st, buf.value.decode())
 
 
 def launch_count() -> int:
