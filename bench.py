@@ -43,6 +43,8 @@ WORKLOADS = {
                            desc="3D 7-point variable-coefficient diffusion, 8x8x4 regions with "
                                 "per-axis node counts from {28,55,82} (seed 1), log-normal "
                                 "per-element kappa (sigma 1), Chebyshev degree 3, 4 levels"),
+    "c2_quarter": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                       desc="C2-shaped 3D 7-point diffusion on 4x4x2 regions (profiling size)"),
     "c1_poisson2d": dict(levels=4, smoother="jacobi", nu1=2, nu2=2, omega=0.67,
                          desc="2D Poisson 5-point, 2x2 regions of 82x82, Jacobi 0.67, nu 2/2, "
                               "4 levels"),
@@ -172,6 +174,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--json-out", default=None, help="also write the JSON line to this file")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -198,7 +201,10 @@ def main():
         dist.init_process_group("nccl")
     dev = f"cuda:{local_rank}"
 
-    p = W.config(args.workload)
+    if args.workload == "c2_quarter":
+        p = W.diffusion3d_7pt(region_grid=(4, 4, 2), choices=(28, 55, 82), seed=1)
+    else:
+        p = W.config(args.workload)
     dp = upload(p, dev)
     stream = torch.cuda.current_stream(local_rank)
     ctx = rmg.Context(local_rank, stream.cuda_stream)
@@ -390,6 +396,9 @@ def main():
                                    "kind": "oracle", "sample": f"failed: {ex}"[:300]}
     if rank == 0:
         print(json.dumps(out))
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(json.dumps(out) + "\n")
     if dist:
         dist.destroy_process_group()
 
