@@ -170,6 +170,67 @@ rmg_status rmg_setup(rmg_layout* layout, const rmg_options* opts, rmg_hier** out
 rmg_status rmg_setup_numeric(rmg_hier* hier);
 void rmg_hier_destroy(rmg_hier* hier);
 
+/*
+ * Interpolation with stored per-node weights (the general transfers of Table 4 "Generic": the
+ * sparsity of 3:1 linear interpolation, coefficients of the caller's choice). wr is device
+ * double[3 * n_r(level)], axis-major: wr[a * n_r + n] is the weight regional fine node n takes
+ * from its right coarse neighbour along axis a (1 - wr from the left one); it is ignored along
+ * axes where n sits on a coarse index. Co-located copies must carry identical weights and
+ * interface nodes may only use interface coarse nodes (Lemma 2); weights computed from
+ * composite data satisfy both. wr = NULL restores linear interpolation. Call
+ * rmg_setup_numeric afterwards (it rebuilds the Galerkin products and, if the kind of
+ * transfer changed, re-captures the V-cycle graph). Levels 0 .. levels-2.
+ */
+rmg_status rmg_hier_set_transfer_weights(rmg_hier* hier, int level, const double* wr);
+/* Operator-dependent weights of a level (device double[3 * n_r], layout as above): along each
+ * axis the fine nodes between two coarse nodes are weighted by the series resistances
+ * 1/(-A_ij) of the three composite couplings on that line (the 1D A-harmonic extension,
+ * linear for constant coefficients; linear where a coupling is not negative). */
+rmg_status rmg_hier_opdep_weights(rmg_hier* hier, int level, double* wr);
+
+/*
+ * Learned prolongator (no counterpart in the paper, which keeps linear interpolation and
+ * notes that matrix-dependent transfers must match at co-located nodes, Sec. 3.2).
+ * A small MLP maps 27 features of a fine node's local composite operator (padded to 32) to
+ * the three per-axis interpolation weights of rmg_hier_set_transfer_weights:
+ *   32 -> 64 (ReLU) -> 64 (ReLU) -> 3 (sigmoid); forward on BF16 tensor cores with FP32
+ *   accumulation, backward in FP32, Adam on FP32 master weights.
+ * Parameters (float[rmg_mlp_num_params()], host): W1[64][32], b1[64], W2[64][64], b2[64],
+ * W3[3][64], b3[3]. Features: float[n][32] row-major (device). Labels and loss mask:
+ * float[n][3] (device); the loss is sum mask (out - label)^2 / (3 n).
+ */
+typedef struct rmg_mlp rmg_mlp;
+int rmg_mlp_num_params(void);
+rmg_status rmg_mlp_create(rmg_ctx* ctx, const float* init_params, rmg_mlp** out);
+void rmg_mlp_destroy(rmg_mlp* mlp);
+/* Copies the current FP32 parameters to host memory (synchronises). */
+rmg_status rmg_mlp_get_params(rmg_mlp* mlp, float* params);
+/* out (device float[n][3]) = network(feats). */
+rmg_status rmg_mlp_forward(rmg_mlp* mlp, int n, const float* feats, float* out);
+/* Loss and gradient over all n samples in order (host outputs; synchronises). */
+rmg_status rmg_mlp_gradient(rmg_mlp* mlp, int n, const float* feats, const float* labels,
+                            const float* mask, float* grad, float* loss);
+/* steps Adam steps (learning rate lr) on batches of `batch` samples (a multiple of 128)
+ * drawn with replacement by a counter-based hash of (seed, step, row); loss_history: host
+ * float[steps] or NULL. Synchronises at the end. */
+rmg_status rmg_mlp_train(rmg_mlp* mlp, int n, const float* feats, const float* labels,
+                         const float* mask, int steps, int batch, float lr,
+                         unsigned long long seed, float* loss_history);
+/* Features of every regional node of a hierarchy level (device float[n_r][32]). */
+rmg_status rmg_hier_mlp_features(rmg_hier* hier, int level, float* feats);
+/* Network inference on a level: per-axis weights (device double[3 * n_r]) for
+ * rmg_hier_set_transfer_weights (zero along axes where a node sits on a coarse index).
+ * Synchronises. */
+rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, double* wr);
+
+/* Measured convergence of the V-cycle as a stationary solver: from a SplitMix64 random
+ * error e (stream `seed`, zero at masked nodes), iterate e <- e - M^-1 A e `iters` times and
+ * return (||e_iters||_A / ||e_0||_A)^(1/iters). Used to label training operators and to
+ * accept or reject learned interpolation. Synchronises once per cycle. Uses the PCG work
+ * vectors of the hierarchy. */
+rmg_status rmg_hier_convergence_factor(rmg_hier* hier, int iters, unsigned long long seed,
+                                       double* factor);
+
 /* One V-cycle with zero initial guess: z = M^-1 r. r and z are device vectors, composite
  * (layout_flag = 0) or regional and consistent (layout_flag = 1). */
 rmg_status rmg_vcycle_apply(rmg_hier* hier, const double* r, double* z, int layout_flag);

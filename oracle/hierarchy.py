@@ -20,7 +20,7 @@ import scipy.sparse as sp
 
 from .regions import Layout, make_layout, block_diag
 from .split import split_regional
-from .transfer import composite_p, coarse_count, coarse_mask_from_fine, regional_p
+from .transfer import composite_p, coarse_count, coarse_mask_from_fine, regional_p, stored_p
 
 
 @dataclass
@@ -64,11 +64,13 @@ def _identity_on_mask(A: sp.csr_matrix, mask_diag_value: np.ndarray) -> sp.csr_m
     return (A + sp.diags(mask_diag_value)).tocsr()
 
 
-def build(problem_or_parts, nlevels: int, regional: bool = True):
+def build(problem_or_parts, nlevels: int, regional: bool = True, weights=None):
     """Build both hierarchies from a composite problem.
 
     ``problem_or_parts`` needs attributes global_dims, region_dims, region_gids, dirichlet, A.
-    Returns a list of Level.
+    ``weights(l, level)``, if given, returns stored interpolation weights (3, n_l) for the
+    transfer from level l (or None for linear interpolation); it is called once the level's
+    operators exist. Returns a list of Level.
     """
     p = problem_or_parts
     dims = tuple(int(v) for v in p.global_dims)
@@ -81,7 +83,12 @@ def build(problem_or_parts, nlevels: int, regional: bool = True):
     for l in range(nlevels - 1):
         f = levels[l]
         cdims, clayout = inject_layout(f.layout, f.dims)
-        P = composite_p(f.dims, f.layout.mask, clayout.mask)
+        wr = weights(l, f) if weights is not None else None
+        if wr is None:
+            P = composite_p(f.dims, f.layout.mask, clayout.mask)
+        else:
+            P = stored_p(f.dims, wr, f.layout.mask, clayout.mask)
+        f.extra["wr"] = wr
         Ac = (P.T @ f.A @ P).tocsr()
         Ac = _identity_on_mask(Ac, clayout.mask.astype(float))
         f.P = P

@@ -1,0 +1,124 @@
+"""Operator-dependent interpolation weights and the small MLP of the learned prolongator.
+
+The paper keeps linear interpolation and notes that matrix-dependent transfers (black box
+multigrid) must produce identical stencils at co-located nodes (Sec. 3.2). The learned
+prolongator predicts per-node, per-axis interpolation weights; its teacher is the
+operator-dependent candidate below, computed from the composite matrix:
+
+  along axis a, a fine node at remainder rem between coarse nodes X0 and X0 + 3 lies on a
+  line of three edges with conductances k_e = -A(p_e, p_e+1); as resistors in series the
+  weight of the right coarse node is sum_{e < rem} (1/k_e) / sum_e (1/k_e) (the 1D
+  A-harmonic extension); rem/3 (linear) when a conductance is not positive.
+
+The MLP functions are a plain FP64 restatement of the network (27 features padded to 32 ->
+64 -> 64 -> 3, ReLU, ReLU, sigmoid) with the BF16 roundings of the GPU forward pass applied
+at the same points, used to check the GPU gradients.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+NFEAT = 32
+H = 64
+NOUT = 3
+
+
+def opdep_weights(A: sp.csr_matrix, global_dims) -> np.ndarray:
+    """(3, n) operator-dependent right weights per composite node and axis."""
+    Nx, Ny, Nz = global_dims
+    n = Nx * Ny * Nz
+    A = sp.csr_matrix(A)
+    g = np.arange(n)
+    coord = [g % Nx, (g // Nx) % Ny, g // (Nx * Ny)]
+    stride = [1, Nx, Nx * Ny]
+    dims = [Nx, Ny, Nz]
+    wr = np.zeros((3, n))
+    for a in range(3):
+        if dims[a] == 1:
+            continue
+        rem = coord[a] % 3
+        act = np.flatnonzero(rem != 0)
+        r = rem[act]
+        p0 = act - r * stride[a]
+        ks = []
+        for e in range(3):
+            i = p0 + e * stride[a]
+            j = i + stride[a]
+            ks.append(-np.asarray(A[i, j]).ravel())
+        k = np.stack(ks)                       # (3, m)
+        good = np.all(k > 0, axis=0)
+        res = np.where(good, 1.0 / np.where(good, k, 1.0), 0.0)
+        tot = res.sum(axis=0)
+        num = np.where(r == 1, res[0], res[0] + res[1])
+        w = np.where(good, num / np.where(good, tot, 1.0), r / 3.0)
+        wr[a, act] = w
+    return wr
+
+
+# ------------------------------------------------------------------------------ MLP
+def bf16_round(x):
+    """Round float32 values to bfloat16 (round to nearest even), returned as float64."""
+    x32 = np.asarray(x, dtype=np.float32)
+    u = x32.view(np.uint32).astype(np.uint64)
+    bias = 0x7FFF + ((u >> 16) & 1)
+    r = ((u + bias) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def unpack(params):
+    p = np.asarray(params, dtype=np.float64)
+    o = 0
+    W1 = p[o:o + H * NFEAT].reshape(H, NFEAT); o += H * NFEAT
+    b1 = p[o:o + H]; o += H
+    W2 = p[o:o + H * H].reshape(H, H); o += H * H
+    b2 = p[o:o + H]; o += H
+    W3 = p[o:o + NOUT * H].reshape(NOUT, H); o += NOUT * H
+    b3 = p[o:o + NOUT]; o += NOUT
+    assert o == p.size
+    return W1, b1, W2, b2, W3, b3
+
+
+NPARAMS = H * NFEAT + H + H * H + H + NOUT * H + NOUT
+
+
+def forward(params, X, rounding=True):
+    """Forward pass with the GPU's BF16 operand roundings (inputs, weights, hidden
+    activations; ``rounding=False`` gives the exact FP64 network), FP64 accumulation.
+    Returns the outputs and the cached activations."""
+    rnd = bf16_round if rounding else (lambda v: np.asarray(v, dtype=np.float64))
+    W1, b1, W2, b2, W3, b3 = unpack(params)
+    Xb = rnd(X)
+    Z1 = Xb @ rnd(W1).T + b1
+    H1 = np.maximum(Z1, 0.0)
+    H1b = rnd(H1)
+    Z2 = H1b @ rnd(W2).T + b2
+    H2 = np.maximum(Z2, 0.0)
+    H2b = rnd(H2)
+    Z3 = H2b @ rnd(W3).T + b3
+    O = 1.0 / (1.0 + np.exp(-Z3))
+    return O, (Xb, H1b, H2b, O)
+
+
+def loss_and_grad(params, X, Y, M, rounding=True):
+    """Masked mean squared error L = sum M (O - Y)^2 / (3 B) and its gradient by the chain
+    rule (ReLU derivative taken where the activation is positive). The backward pass uses
+    FP32 weights for the data gradients, as the GPU does."""
+    W1, b1, W2, b2, W3, b3 = unpack(params)
+    B = X.shape[0]
+    O, (Xb, H1b, H2b, _) = forward(params, X, rounding)
+    L = float(np.sum(M * (O - Y) ** 2) / (NOUT * B))
+    dO = 2.0 * M * (O - Y) / (NOUT * B)
+    dZ3 = dO * O * (1.0 - O)
+    dW3 = dZ3.T @ H2b
+    db3 = dZ3.sum(axis=0)
+    dH2 = dZ3 @ W3
+    dZ2 = dH2 * (H2b > 0)
+    dW2 = dZ2.T @ H1b
+    db2 = dZ2.sum(axis=0)
+    dH1 = dZ2 @ W2
+    dZ1 = dH1 * (H1b > 0)
+    dW1 = dZ1.T @ Xb
+    db1 = dZ1.sum(axis=0)
+    grad = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
+    return L, grad

@@ -55,6 +55,48 @@ def composite_p(global_dims, fine_mask, coarse_mask) -> sp.csr_matrix:
     return P
 
 
+def stored_p(global_dims, wr, fine_mask, coarse_mask) -> sp.csr_matrix:
+    """P with stored per-node weights (Table 4's "general grid transfers": the sparsity of 3:1
+    linear interpolation with coefficients of choice).
+
+    ``wr`` is (3, n_fine): the weight fine node f takes from its right coarse neighbour along
+    axis a; the left neighbour gets 1 - wr; along an axis where f sits on a coarse index the
+    weight is 1. The row is the tensor product of the three axis weights.
+    """
+    Nx, Ny, Nz = global_dims
+    cNx, cNy, cNz = coarse_count(Nx), coarse_count(Ny), coarse_count(Nz)
+    n = Nx * Ny * Nz
+    g = np.arange(n)
+    coord = [g % Nx, (g // Nx) % Ny, g // (Nx * Ny)]
+    c0 = [c // 3 for c in coord]
+    rem = [c - 3 * q for c, q in zip(coord, c0)]
+    rows, cols, vals = [], [], []
+    for sc in (0, 1):
+        for sb in (0, 1):
+            for sa in (0, 1):
+                side = (sa, sb, sc)
+                ok = np.ones(n, bool)
+                w = np.ones(n)
+                cc = []
+                for a in range(3):
+                    if side[a]:
+                        ok &= rem[a] != 0
+                        wa = np.where(rem[a] != 0, wr[a], 0.0)
+                    else:
+                        wa = np.where(rem[a] != 0, 1.0 - np.asarray(wr[a]), 1.0)
+                    cc.append(c0[a] + side[a])
+                    w = w * wa if a == 0 else wa * w
+                col = cc[0] + cNx * (cc[1] + cNy * cc[2])
+                rows.append(g[ok]); cols.append(col[ok]); vals.append(w[ok])
+    P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, cNx * cNy * cNz))
+    keep_rows = sp.diags((~np.asarray(fine_mask, bool)).astype(float))
+    keep_cols = sp.diags((~np.asarray(coarse_mask, bool)).astype(float))
+    P = (keep_rows @ P @ keep_cols).tocsr()
+    P.eliminate_zeros()
+    return P
+
+
 def coarse_dims(global_dims):
     return tuple(coarse_count(n) for n in global_dims)
 

@@ -251,6 +251,28 @@ rmg_status rmg_hier_level_export(rmg_hier* hh, int level, double* coeffs, double
   });
 }
 
+rmg_status rmg_hier_set_transfer_weights(rmg_hier* hh, int level, const double* wr) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] { set_transfer_weights(hh->h, level, wr); });
+}
+
+rmg_status rmg_hier_opdep_weights(rmg_hier* hh, int level, double* wr) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(wr, RMG_ERR_ARG, "wr is NULL");
+    opdep_weights(hh->h, level, wr);
+  });
+}
+
+rmg_status rmg_hier_convergence_factor(rmg_hier* hh, int iters, unsigned long long seed,
+                                       double* factor) {
+  if (!hh || !factor) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(iters > 0, RMG_ERR_ARG, "iters must be positive");
+    *factor = convergence_factor(hh->h, iters, seed);
+  });
+}
+
 rmg_status rmg_hier_lambda(rmg_hier* hh, int level, double* lam) {
   if (!hh || !lam) return RMG_ERR_ARG;
   Hier& h = hh->h;

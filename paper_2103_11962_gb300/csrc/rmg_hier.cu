@@ -93,6 +93,11 @@ k_cg_update(int n, const double* __restrict__ p, const double* __restrict__ q,
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__global__ void k_axpy_neg(int n, const double* __restrict__ z, double* __restrict__ e) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    e[k] -= z[k];
+}
+
 __global__ void k_p_update(int n, const double* __restrict__ z, const Scalars* __restrict__ sc,
                            double* __restrict__ p) {
   const double b = sc->beta;
@@ -210,12 +215,23 @@ struct Exec {
   // [[Psi Psi^T]]^-1 scaling of the restriction
   void residual(int l) { stencil(l, cur[l], EpiResidScaled<VT>{V(l).b.get(), V(l).r.get()}); }
 
+  const VT* pw(int l) const;
+
   void restrict_to(int l) {
     const Level& F = *h.lv[l];
     const Level& C = *h.lv[l + 1];
     const Grid Gc = C.grid();
     const int gb = persistent_grid(c(), Gc.ntiles);
-    if (F.dim == 3)
+    if (F.stored_p) {
+      if (F.dim == 3)
+        k_restrict_w<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), F.n_r, pw(l), V(l).r.get(),
+                                                  C.mask.get(), C.mult.get(), V(l + 1).b.get(),
+                                                  V(l + 1).y.get());
+      else
+        k_restrict_w<2, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), F.n_r, pw(l), V(l).r.get(),
+                                                  C.mask.get(), C.mult.get(), V(l + 1).b.get(),
+                                                  V(l + 1).y.get());
+    } else if (F.dim == 3)
       k_restrict<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), V(l).r.get(), C.mask.get(),
                                               C.mult.get(), V(l + 1).b.get(), V(l + 1).y.get());
     else
@@ -236,7 +252,14 @@ struct Exec {
     const Level& C = *h.lv[l + 1];
     const Grid Gf = F.grid();
     const int gb = persistent_grid(c(), Gf.ntiles);
-    if (F.dim == 3)
+    if (F.stored_p) {
+      if (F.dim == 3)
+        k_prolong_w<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), pw(l), F.mask.get(),
+                                                 cur[l + 1], cur[l]);
+      else
+        k_prolong_w<2, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), pw(l), F.mask.get(),
+                                                 cur[l + 1], cur[l]);
+    } else if (F.dim == 3)
       k_prolong<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), F.mask.get(), cur[l + 1], cur[l]);
     else
       k_prolong<2, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), F.mask.get(), cur[l + 1], cur[l]);
@@ -287,6 +310,9 @@ struct Exec {
   }
 };
 
+template <> const double* Exec<double, double>::pw(int l) const { return h.lv[l]->pw.get(); }
+template <> const float* Exec<float, float>::pw(int l) const { return h.lv[l]->pw32.get(); }
+template <> const float* Exec<float, __nv_bfloat16>::pw(int l) const { return h.lv[l]->pw32.get(); }
 template <> LevelVecs<double>& Exec<double, double>::V(int l) { return h.v64[l]; }
 template <> const double* Exec<double, double>::coef(int l) const { return h.lv[l]->coef.get(); }
 template <> const double* Exec<double, double>::dinv(int l) const { return h.lv[l]->dinv.get(); }
@@ -461,16 +487,78 @@ static void galerkin(Hier& h, const Level& F, Level& C) {
   RMG_LAUNCHED();                                                                             \
   k_rtap<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, C.mask.get(),     \
                                             C.mult.get(), C.coef.get())
-  switch (F.kind) {
-    case 5: RMG_RAP(5, 9, 2); break;
-    case 9: RMG_RAP(9, 9, 2); break;
-    case 7: RMG_RAP(7, 27, 3); break;
-    default: RMG_RAP(27, 27, 3); break;
+#define RMG_RAPW(FK, CK, D)                                                                   \
+  {                                                                                           \
+    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
+    RMG_CUDA(cudaFuncSetAttribute(k_ap_w<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                  smem));                                                     \
+    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), F.pw.get(), \
+                                                 F.mask.get(), C.mask.get(), ap);             \
+  }                                                                                           \
+  RMG_LAUNCHED();                                                                             \
+  k_rtap_w<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, F.pw.get(),     \
+                                              C.mask.get(), C.mult.get(), C.coef.get())
+  if (F.stored_p) {
+    switch (F.kind) {
+      case 5: RMG_RAPW(5, 9, 2); break;
+      case 9: RMG_RAPW(9, 9, 2); break;
+      case 7: RMG_RAPW(7, 27, 3); break;
+      default: RMG_RAPW(27, 27, 3); break;
+    }
+  } else {
+    switch (F.kind) {
+      case 5: RMG_RAP(5, 9, 2); break;
+      case 9: RMG_RAP(9, 9, 2); break;
+      case 7: RMG_RAP(7, 27, 3); break;
+      default: RMG_RAP(27, 27, 3); break;
+    }
   }
 #undef RMG_RAP
+#undef RMG_RAPW
   RMG_LAUNCHED();
 }
 
+// Stored transfer weights for level -> level+1 (NULL restores linear interpolation). The
+// numeric setup must run afterwards; it re-captures the V-cycle graph when the kind of
+// transfer of a level changed.
+void set_transfer_weights(Hier& h, int level, const double* wr) {
+  RMG_REQUIRE(level >= 0 && level + 1 < h.levels(), RMG_ERR_ARG,
+              "transfer weights exist for levels 0 .. levels-2");
+  Level& L = *h.lv[level];
+  if (!wr) {
+    L.stored_p = false;
+    return;
+  }
+  L.pw.ensure((size_t)3 * L.n_r);
+  RMG_CUDA(cudaMemcpyAsync(L.pw.get(), wr, L.pw.bytes(), cudaMemcpyDeviceToDevice, h.c->stream));
+  if (h.mixed()) L.pw32.ensure((size_t)3 * L.n_r);
+  L.stored_p = true;
+}
+
+// Operator-dependent (series-resistance) weights of a level from its current operator.
+void opdep_weights(Hier& h, int level, double* wr) {
+  RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
+  Level& L = *h.lv[level];
+  Ctx& c = *h.c;
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+#define RMG_OPD(K)                                                                             \
+  k_opdep<K><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), L.mult.get(), L.gid.get(),           \
+                                         L.cgrp.get(), L.gptr.get(), L.gslot.get(), wr)
+  switch (L.kind) {
+    case 5: RMG_OPD(5); break;
+    case 7: RMG_OPD(7); break;
+    case 9: RMG_OPD(9); break;
+    default: RMG_OPD(27); break;
+  }
+#undef RMG_OPD
+  RMG_LAUNCHED();
+}
+
+// lambda~_max(D~^-1 A) by the power method (Sec. 3.4). The start vector is normalised once;
+// the power_iters steps y <- D~^-1 A y then run without normalising (the direction is the
+// same as with a normalisation per step, and ||D~^-1 A|| <= 2 bounds the growth), and the
+// estimate is the Rayleigh quotient y^T D~^-1 A y / y^T y of the last iterate.
 static void power_method(Hier& h, int l) {
   Ctx& c = *h.c;
   Level& L = *h.lv[l];
@@ -484,17 +572,17 @@ static void power_method(Hier& h, int l) {
   dot(c, n, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
   k_scale_div<<<eg, 256, 0, st>>>(n, V.u.get(), &sc->pw_norm, V.u.get());
   RMG_LAUNCHED();
+  double* a = V.u.get();
+  double* b = V.r.get();
   for (int it = 0; it < h.o.power_iters; ++it) {
-    launch_stencil(c, L, L.coef.get(), V.u.get(), V.y.get(),
-                   EpiScaled<double>{L.dinv.get(), V.r.get()}, st, nullptr);
-    dot(c, n, V.r.get(), V.r.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
-    k_scale_div<<<eg, 256, 0, st>>>(n, V.r.get(), &sc->pw_norm, V.u.get());
-    RMG_LAUNCHED();
+    launch_stencil(c, L, L.coef.get(), a, V.y.get(), EpiScaled<double>{L.dinv.get(), b}, st,
+                   nullptr);
+    std::swap(a, b);
   }
-  launch_stencil(c, L, L.coef.get(), V.u.get(), V.y.get(),
-                 EpiScaled<double>{L.dinv.get(), V.r.get()}, st, nullptr);
-  dot(c, n, V.u.get(), V.r.get(), L.mult.get(), &sc->pw_num, FIN_STORE, st);
-  dot(c, n, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_den, FIN_STORE, st);
+  launch_stencil(c, L, L.coef.get(), a, V.y.get(), EpiScaled<double>{L.dinv.get(), b}, st,
+                 nullptr);
+  dot(c, n, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
+  dot(c, n, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
   k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
   RMG_LAUNCHED();
 }
@@ -559,6 +647,11 @@ static void make_low_precision(Hier& h) {
     RMG_LAUNCHED();
     k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.n_r, L.dinv.get(), L.dinv32.get());
     RMG_LAUNCHED();
+    if (L.stored_p) {
+      L.pw32.ensure((size_t)3 * L.n_r);
+      k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)3 * L.n_r, L.pw.get(), L.pw32.get());
+      RMG_LAUNCHED();
+    }
   }
 }
 
@@ -584,8 +677,17 @@ void hier_numeric(Hier& h) {
   if (h.mixed()) make_low_precision(h);
   RMG_CUDA(cudaMemcpyAsync(&h.hsc, h.sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<char> stored(Lv);
+  for (int l = 0; l < Lv; ++l) stored[l] = h.lv[l]->stored_p ? 1 : 0;
+  if (h.gexec && stored != h.graph_stored) {
+    cudaGraphExecDestroy(h.gexec);
+    cudaGraphDestroy(h.graph);
+    h.gexec = nullptr;
+    h.graph = nullptr;
+  }
+  h.graph_stored = stored;
   if (h.o.use_graph && !h.gexec) {
-    RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
+    if (!h.graph_stream) RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
     RMG_CUDA(cudaStreamBeginCapture(h.graph_stream, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
     g_capturing = true;
@@ -650,6 +752,47 @@ void probe_collect(Hier& h) {
     cudaGetLastError();
   }
   h.probe_pending = false;
+}
+
+// V-cycle as a stationary solver on A e = 0 from a SplitMix64 random error:
+// e <- e - M^-1 A e. Returns (||e_K||_A / ||e_0||_A)^(1/K), the mean A-norm error reduction
+// per cycle (FP64 A-norm; the cycle in the hierarchy's own precision).
+double convergence_factor(Hier& h, int iters, unsigned long long seed) {
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  const Level& L0 = *h.lv[0];
+  const int n = L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  Scalars* sc = h.sc.get();
+  double* e = h.x.get();
+  double* Ae = h.v64[0].b.get();      // the cycle's right-hand side buffer
+  double* z = h.v64[0].u.get();
+  k_power_init<<<eg, 256, 0, st>>>(n, L0.gid.get(), L0.mask.get(), seed, e);
+  RMG_LAUNCHED();
+  auto anorm2 = [&]() {
+    launch_stencil(c, L0, L0.coef.get(), e, h.v64[0].y.get(), EpiStore<double>{Ae}, st, nullptr);
+    dot(c, n, e, Ae, L0.mult.get(), &sc->pq, FIN_STORE, st);
+    RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->pq, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RMG_CUDA(cudaStreamSynchronize(st));
+    return h.pinned[0];
+  };
+  const double e0 = anorm2();
+  double ek = e0;
+  for (int k = 0; k < iters; ++k) {
+    if (h.mixed()) {
+      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, Ae, h.v32[0].b.get());
+      RMG_LAUNCHED();
+      vcycle(h);
+      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, h.v32[0].u.get(), z);
+      RMG_LAUNCHED();
+    } else {
+      vcycle(h);
+    }
+    k_axpy_neg<<<eg, 256, 0, st>>>(n, z, e);
+    RMG_LAUNCHED();
+    ek = anorm2();
+  }
+  if (!(e0 > 0.0) || iters <= 0) return 0.0;
+  return std::pow(std::max(ek, 0.0) / e0, 0.5 / iters);
 }
 
 // ---------------------------------------------------------------------- PCG

@@ -179,6 +179,11 @@ struct Level {
   DBuf<float> coef32;
   DBuf<__nv_bfloat16> coef16;
   DBuf<float> dinv32;
+  // stored transfer weights to the next coarser level (linear 3:1 when not stored):
+  // pw[a * n_r + n] = weight of the right coarse neighbour along axis a
+  bool stored_p = false;
+  DBuf<double> pw;
+  DBuf<float> pw32;
 
   Grid grid() const { return Grid{regions.get(), tiles.get(), (int)htiles.size(), nreg, n_r}; }
 };

@@ -294,6 +294,98 @@ k_prolong(Grid Gf, const RegionDev* __restrict__ cregions, const uint8_t* __rest
   RMG_END_FOR_NODES
 }
 
+// ---- transfers with stored per-node weights ------------------------------------------
+// wr[a * n_f + f] is the weight fine node f takes from its right coarse neighbour along axis a
+// (the left one gets 1 - wr); along an axis where f sits on a coarse index the weight is 1.
+// Seen from coarse node C, the fine node f = 3C + offset carries, per axis, 1 for offset 0,
+// 1 - wr for offsets 1, 2 (C is f's left neighbour) and wr for offsets -1, -2.
+template <typename T, typename W>
+__device__ __forceinline__ T pw_seen_from_coarse(const W* __restrict__ wr, int n_f, int f,
+                                                 int axis, int off) {
+  return off == 0 ? T(1) : (off > 0 ? T(1) - T(wr[(size_t)axis * n_f + f])
+                                    : T(wr[(size_t)axis * n_f + f]));
+}
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kTile)
+k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const VT* __restrict__ wr,
+             const VT* __restrict__ rs, const uint8_t* __restrict__ cmask,
+             const uint8_t* __restrict__ cmult, VT* __restrict__ w, VT* __restrict__ yc) {
+  RMG_FOR_NODES(Gc)
+    int I, J, L;
+    decode(li, R, I, J, L);
+    VT acc = VT(0);
+    if (!cmask[n]) {
+      const RegionDev F = fregions[tile_.region];
+      const int zl = DIM == 3 ? -2 : 0, zh = DIM == 3 ? 2 : 0;
+      for (int c = zl; c <= zh; ++c) {
+        const int fz = DIM == 3 ? 3 * L + c : 0;
+        if (fz < 0 || fz >= F.nz) continue;
+        for (int b = -2; b <= 2; ++b) {
+          const int fy = 3 * J + b;
+          if (fy < 0 || fy >= F.ny) continue;
+          for (int a = -2; a <= 2; ++a) {
+            const int fx = 3 * I + a;
+            if (fx < 0 || fx >= F.nx) continue;
+            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
+            const VT wz = DIM == 3 ? pw_seen_from_coarse<VT>(wr, fn_r, f, 2, c) : VT(1);
+            const VT wgt = wz * (pw_seen_from_coarse<VT>(wr, fn_r, f, 1, b) *
+                                 pw_seen_from_coarse<VT>(wr, fn_r, f, 0, a));
+            acc = fma(wgt, rs[f], acc);
+          }
+        }
+      }
+    }
+    if (cmult[n] > 1) yc[n] = acc; else w[n] = acc;
+  RMG_END_FOR_NODES
+}
+
+template <int DIM, typename VT>
+__global__ void __launch_bounds__(kTile)
+k_prolong_w(Grid Gf, const RegionDev* __restrict__ cregions, const VT* __restrict__ wr,
+            const uint8_t* __restrict__ fmask, const VT* __restrict__ ubar, VT* __restrict__ u) {
+  RMG_FOR_NODES(Gf)
+    if (fmask[n]) continue;
+    int i, j, l;
+    decode(li, R, i, j, l);
+    const RegionDev C = cregions[tile_.region];
+    const int co[3] = {i / 3, j / 3, DIM == 3 ? l / 3 : 0};
+    const int rm[3] = {i - 3 * co[0], j - 3 * co[1], DIM == 3 ? l - 3 * co[2] : 0};
+    VT w0[3], w1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const VT r = rm[a] ? VT(wr[(size_t)a * Gf.n_r + n]) : VT(0);
+      w0[a] = VT(1) - r;
+      w1[a] = r;
+    }
+    const int base = C.off + co[0] + C.nx * (co[1] + C.ny * co[2]);
+    VT acc = VT(0);
+    for (int c = 0; c < (rm[2] ? 2 : 1); ++c)
+      for (int b = 0; b < (rm[1] ? 2 : 1); ++b)
+        for (int a = 0; a < (rm[0] ? 2 : 1); ++a) {
+          const VT wgt = (c ? w1[2] : w0[2]) * ((b ? w1[1] : w0[1]) * (a ? w1[0] : w0[0]));
+          acc = fma(wgt, ubar[base + a + C.nx * (b + C.ny * c)], acc);
+        }
+    u[n] = u[n] + acc;
+  RMG_END_FOR_NODES
+}
+
+// Composite coupling of regional node n in stencil slot `slot`: the sum over the copies of
+// the node (a copy in a region without that neighbour contributes zero).
+template <int KIND>
+__device__ __forceinline__ double comp_coupling(const double* __restrict__ coef, int n_r, int n,
+                                                int slot, const uint8_t* __restrict__ mult,
+                                                const int* __restrict__ gid,
+                                                const int* __restrict__ cgrp,
+                                                const int* __restrict__ gptr,
+                                                const int* __restrict__ gslot) {
+  if (mult[n] == 1) return coef[(size_t)slot * n_r + n];
+  const int grp = cgrp[gid[n]];
+  double s = 0.0;
+  for (int q = gptr[grp]; q < gptr[grp + 1]; ++q) s += coef[(size_t)slot * n_r + gslot[q]];
+  return s;
+}
+
 // ------------------------------------------------------------------ reductions
 // Deterministic two-pass reductions: every block writes one partial sum; a single block
 // adds the partials in order.

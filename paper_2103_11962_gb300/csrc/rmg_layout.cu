@@ -348,13 +348,13 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
       const int slot = sten_slot<KIND>(ic - i, jc - j, lc - l);
       if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
       const int q = share_count(g, c, G.regions, G.nreg, cgrp, gptr, gslot);
-      const double vs = v / (double)q;
+      const double vs = v * inv_mult<double>(q);
       offsum += vs;
 #pragma unroll
       for (int s = 0; s < S::S; ++s)
         if (s == slot) acc[s] += vs;
     }
-    acc[S::CENTER] = zsum / (double)mult[n] - offsum;
+    acc[S::CENTER] = zsum * inv_mult<double>(mult[n]) - offsum;
 #pragma unroll
     for (int s = 0; s < S::S; ++s) coef[(size_t)s * G.n_r + n] = acc[s];
   RMG_END_FOR_NODES

@@ -187,6 +187,152 @@ k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ 
   RMG_END_FOR_NODES
 }
 
+// Galerkin product with stored per-node weights (same two steps as k_ap / k_rtap).
+template <int FK, int DIM>
+__global__ void __launch_bounds__(kTile)
+k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fcoef,
+       const double* __restrict__ wr, const uint8_t* __restrict__ fmask,
+       const uint8_t* __restrict__ cmask, double* __restrict__ ap) {
+  using FS = Sten<FK>;
+  constexpr int NO = DIM == 3 ? 27 : 9;
+  extern __shared__ double ap_acc[];
+  double (*acc)[kTile] = reinterpret_cast<double (*)[kTile]>(ap_acc);
+  const int tid = threadIdx.x;
+  RMG_FOR_NODES(Gf)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o][tid] = 0.0;
+    if (!fmask[n]) {
+      int x, y, z;
+      decode(li, R, x, y, z);
+      const RegionDev C = cregs[tile_.region];
+      const int cx0 = floor_div3m1(x), cy0 = floor_div3m1(y), cz0 = DIM == 3 ? floor_div3m1(z) : 0;
+#pragma unroll
+      for (int s = 0; s < FS::S; ++s) {
+        const int gx = x + FS::dx(s), gy = y + FS::dy(s), gz = z + FS::dz(s);
+        if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
+        const double v = fcoef[(size_t)s * Gf.n_r + n];
+        if (v == 0.0) continue;
+        const int f2 = R.off + gx + R.nx * (gy + R.ny * gz);
+        if (fmask[f2]) continue;
+        const int x0 = gx / 3, rx = gx - 3 * x0;
+        const int y0 = gy / 3, ry = gy - 3 * y0;
+        const int z0 = DIM == 3 ? gz / 3 : 0, rz = DIM == 3 ? gz - 3 * z0 : 0;
+        const double wx = rx ? wr[f2] : 0.0;
+        const double wy = ry ? wr[(size_t)Gf.n_r + f2] : 0.0;
+        const double wz = rz ? wr[(size_t)2 * Gf.n_r + f2] : 0.0;
+        for (int c = 0; c < (rz ? 2 : 1); ++c)
+          for (int b = 0; b < (ry ? 2 : 1); ++b)
+            for (int a = 0; a < (rx ? 2 : 1); ++a) {
+              const int X = x0 + a, Y = y0 + b, Z = z0 + c;
+              if (cmask[C.off + X + C.nx * (Y + C.ny * Z)]) continue;
+              const double wgt = (c ? wz : 1.0 - wz) * ((b ? wy : 1.0 - wy) * (a ? wx : 1.0 - wx));
+              const int o = (X - cx0) + 3 * (Y - cy0) + 9 * (Z - cz0);
+              acc[o][tid] = fma(v, wgt, acc[o][tid]);
+            }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) ap[(size_t)o * Gf.n_r + n] = acc[o][tid];
+  RMG_END_FOR_NODES
+}
+
+template <int CK, int DIM>
+__global__ void __launch_bounds__(kTile)
+k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
+         const double* __restrict__ wr, const uint8_t* __restrict__ cmask,
+         const uint8_t* __restrict__ cmult, double* __restrict__ ccoef) {
+  using CS = Sten<CK>;
+  RMG_FOR_NODES(Gc)
+    double acc[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+    if (cmask[n]) {
+      acc[DIM == 3 ? 13 : 4] = 1.0 / (double)cmult[n];
+    } else {
+      int I, J, L;
+      decode(li, R, I, J, L);
+      const RegionDev F = fregs[tile_.region];
+      for (int c = (DIM == 3 ? -2 : 0); c <= (DIM == 3 ? 2 : 0); ++c) {
+        const int fz = DIM == 3 ? 3 * L + c : 0;
+        if (fz < 0 || fz >= F.nz) continue;
+        for (int b = -2; b <= 2; ++b) {
+          const int fy = 3 * J + b;
+          if (fy < 0 || fy >= F.ny) continue;
+          for (int a = -2; a <= 2; ++a) {
+            const int fx = 3 * I + a;
+            if (fx < 0 || fx >= F.nx) continue;
+            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
+            const double wz = DIM == 3 ? pw_seen_from_coarse<double>(wr, fn_r, f, 2, c) : 1.0;
+            const double wf = wz * (pw_seen_from_coarse<double>(wr, fn_r, f, 1, b) *
+                                    pw_seen_from_coarse<double>(wr, fn_r, f, 0, a));
+            if (wf == 0.0) continue;
+            const int bx = a <= 0 ? 1 : 0, by = b <= 0 ? 1 : 0, bz = DIM == 3 ? (c <= 0 ? 1 : 0) : 0;
+#pragma unroll
+            for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
+#pragma unroll
+              for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+                for (int ox = -1; ox <= 1; ++ox) {
+                  const int ix = ox + bx, iy = oy + by, iz = oz + bz;
+                  if (ix < 0 || ix > 2 || iy < 0 || iy > 2 || iz < 0 || iz > 2) continue;
+                  const int slot = (ox + 1) + 3 * (oy + 1) + (DIM == 3 ? 9 * (oz + 1) : 0);
+                  acc[slot] = fma(wf, ap[(size_t)(ix + 3 * iy + 9 * iz) * fn_r + f], acc[slot]);
+                }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
+  RMG_END_FOR_NODES
+}
+
+// ---- operator-dependent interpolation weights (teacher of the learned prolongator) ----
+// Along each axis a fine node between coarse nodes X0 and X0 + 3 lies on a line of three
+// edges with composite conductances k_i = -A(p_i, p_i+1). Treating the line as resistors in
+// series (the 1D A-harmonic extension), the weight of the right coarse node at position rem
+// is (1/k_0 + ... + 1/k_{rem-1}) / (1/k_0 + 1/k_1 + 1/k_2). With equal conductances this is
+// rem/3, the linear weight; with a non-positive conductance the linear weight is kept.
+// Composite couplings are the sums over the copies of a node, so co-located copies obtain
+// identical weights (the matching condition of Lemma 2).
+template <int KIND>
+__global__ void __launch_bounds__(kTile)
+k_opdep(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ mult,
+        const int* __restrict__ gid, const int* __restrict__ cgrp, const int* __restrict__ gptr,
+        const int* __restrict__ gslot, double* __restrict__ wr) {
+  constexpr int DIM = Sten<KIND>::DIM;
+  RMG_FOR_NODES(G)
+    int x[3];
+    decode(li, R, x[0], x[1], x[2]);
+    const int stride[3] = {1, R.nx, R.nx * R.ny};
+    const int len[3] = {R.nx, R.ny, R.nz};
+    for (int a = 0; a < 3; ++a) {
+      int rem = (a < DIM) ? x[a] % 3 : 0;
+      if (rem && x[a] - rem + 3 > len[a] - 1) rem = 0;   // no right coarse node in the region
+      double w = 0.0;
+      if (rem) {
+        const int slot = sten_slot<KIND>(a == 0, a == 1, a == 2);   // coupling to +e_a
+        const int p0 = n - rem * stride[a];
+        double rsum[3];
+        bool ok = slot >= 0;
+        for (int e = 0; e < 3 && ok; ++e) {
+          const double k = -comp_coupling<KIND>(coef, G.n_r, p0 + e * stride[a], slot, mult, gid,
+                                                cgrp, gptr, gslot);
+          if (!(k > 0.0)) ok = false;
+          else rsum[e] = 1.0 / k;
+        }
+        if (ok) {
+          const double tot = rsum[0] + rsum[1] + rsum[2];
+          w = (rem == 1 ? rsum[0] : rsum[0] + rsum[1]) / tot;
+        } else {
+          w = rem / 3.0;
+        }
+      }
+      wr[(size_t)a * G.n_r + n] = w;
+    }
+  RMG_END_FOR_NODES
+}
+
 // ------------------------------------------------------------------ power method (Sec. 3.4)
 // SplitMix64 as a counter-based generator: value i of stream seed = output i+1 of a
 // generator seeded with seed (Steele, Lea, Flood 2014). Doubles in [-1, 1) from the top 53 bits.

@@ -87,6 +87,20 @@ def lib():
         "rmg_hier_coarse_matrix": (ctypes.c_int, [P, I64P, P, P]),
         "rmg_hier_vcycle_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_launch_count": (ctypes.c_ulonglong, []),
+        "rmg_hier_set_transfer_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "rmg_hier_opdep_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "rmg_hier_convergence_factor": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_ulonglong,
+                                                       ctypes.POINTER(ctypes.c_double)]),
+        "rmg_mlp_num_params": (ctypes.c_int, []),
+        "rmg_mlp_create": (ctypes.c_int, [P, P, ctypes.POINTER(P)]),
+        "rmg_mlp_destroy": (None, [P]),
+        "rmg_mlp_get_params": (ctypes.c_int, [P, P]),
+        "rmg_mlp_forward": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+        "rmg_mlp_gradient": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P]),
+        "rmg_mlp_train": (ctypes.c_int, [P, ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_float, ctypes.c_ulonglong, P]),
+        "rmg_hier_mlp_features": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "rmg_hier_mlp_weights": (ctypes.c_int, [P, ctypes.c_int, P, P]),
         "rmg_regional_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
                                                      P, P, ctypes.c_int64, P, P, P,
                                                      ctypes.c_char_p, ctypes.c_int]),
@@ -110,7 +124,10 @@ def exported_symbols():
             "rmg_hier_destroy", "rmg_vcycle_apply", "rmg_pcg_solve", "rmg_hier_level_sizes",
             "rmg_hier_level_export", "rmg_hier_lambda", "rmg_hier_coarse_matrix",
             "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
-            "rmg_regional_apply_static"]
+            "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
+            "rmg_hier_opdep_weights", "rmg_hier_convergence_factor", "rmg_mlp_num_params", "rmg_mlp_create",
+            "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
+            "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
 
 
 def regional_apply_static(dim, region_dims, stencil, coeffs, region_gids, n_composite, u, y,
@@ -290,6 +307,27 @@ class Hierarchy:
                                                         ids.ctypes.data_as(P)))
         return dense, ids
 
+    def set_transfer_weights(self, level, wr):
+        """Stored per-node interpolation weights for level -> level+1 (None = linear)."""
+        self.ctx.check(lib().rmg_hier_set_transfer_weights(self.h, level, _ptr(wr)))
+
+    def opdep_weights(self, level, wr):
+        """Operator-dependent (series-resistance) weights of a level into wr (3 * n_r)."""
+        self.ctx.check(lib().rmg_hier_opdep_weights(self.h, level, _ptr(wr)))
+
+    def convergence_factor(self, iters=6, seed=7):
+        """Mean A-norm error reduction per V-cycle, measured as a stationary solver."""
+        v = ctypes.c_double()
+        self.ctx.check(lib().rmg_hier_convergence_factor(self.h, int(iters), int(seed),
+                                                         ctypes.byref(v)))
+        return v.value
+
+    def mlp_features(self, level, feats):
+        self.ctx.check(lib().rmg_hier_mlp_features(self.h, level, _ptr(feats)))
+
+    def mlp_weights(self, level, mlp, wr):
+        self.ctx.check(lib().rmg_hier_mlp_weights(self.h, level, mlp.h, _ptr(wr)))
+
     def probe(self, reset=True):
         """(total ms, launches) of the timed level-0 smoother kernel since the last reset."""
         ms, n = ctypes.c_double(), ctypes.c_longlong()
@@ -305,6 +343,57 @@ class Hierarchy:
     def close(self):
         if getattr(self, "h", None):
             lib().rmg_hier_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned prolongator's network (parameters live on the device)."""
+
+    def __init__(self, ctx: Context, init_params):
+        self.ctx = ctx
+        p = np.ascontiguousarray(np.asarray(init_params, dtype=np.float32))
+        if p.size != lib().rmg_mlp_num_params():
+            raise ValueError("wrong parameter count")
+        h = P()
+        ctx.check(lib().rmg_mlp_create(ctx.h, p.ctypes.data_as(P), ctypes.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def num_params():
+        return int(lib().rmg_mlp_num_params())
+
+    def params(self):
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        self.ctx.check(lib().rmg_mlp_get_params(self.h, out.ctypes.data_as(P)))
+        return out
+
+    def forward(self, feats, out):
+        self.ctx.check(lib().rmg_mlp_forward(self.h, int(feats.shape[0]), _ptr(feats), _ptr(out)))
+
+    def gradient(self, feats, labels, mask):
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        loss = ctypes.c_float()
+        self.ctx.check(lib().rmg_mlp_gradient(self.h, int(feats.shape[0]), _ptr(feats),
+                                              _ptr(labels), _ptr(mask), g.ctypes.data_as(P),
+                                              ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def train(self, feats, labels, mask, steps, batch=16384, lr=1e-3, seed=0):
+        hist = np.zeros(steps, dtype=np.float32)
+        self.ctx.check(lib().rmg_mlp_train(self.h, int(feats.shape[0]), _ptr(feats), _ptr(labels),
+                                           _ptr(mask), int(steps), int(batch), float(lr),
+                                           int(seed), hist.ctypes.data_as(P)))
+        return hist
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rmg_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,181 @@
+"""Learned prolongator on the GPU: operator-dependent weights, stored-weight transfers, the
+MLP's forward and gradient against the oracle, and the trained network against the plain
+method."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import matrix_rel_diff, rel_max, stencils_to_matrix
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2103_11962_gb300 import rmg
+    return rmg.Context(0)
+
+
+def _hc(seed=13, grid=(3, 2, 2), choices=(10, 19)):
+    return W.highcontrast3d_7pt(region_grid=grid, choices=choices, seed=seed)
+
+
+def _setup(ctx, p, levels=3, smoother="chebyshev"):
+    from paper_2103_11962_gb300 import learned, rmg, upload
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    h = rmg.Hierarchy(lay, learned._options(levels, smoother))
+    return dp, lay, h
+
+
+def _opts(smoother):
+    from oracle import cycle
+    if smoother == "jacobi":
+        return cycle.Options(smoother="jacobi", nu1=2, nu2=2, omega=0.67)
+    return cycle.Options(smoother="chebyshev", nu1=1, nu2=1, degree=3)
+
+
+def test_opdep_weights_match_oracle(ctx):
+    from oracle.learned import opdep_weights
+    for p in (_hc(), W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=5)):
+        dp, lay, h = _setup(ctx, p)
+        n_r = lay.sizes()["n_regional"]
+        wr = torch.empty(3 * n_r, dtype=torch.float64, device="cuda")
+        h.opdep_weights(0, wr)
+        got = wr.view(3, n_r).cpu().numpy()
+        expect = opdep_weights(p.A, p.global_dims)[:, p.region_gids]
+        free = ~p.dirichlet.astype(bool)[p.region_gids]
+        assert np.abs(got[:, free] - expect[:, free]).max() <= 1e-12
+
+
+def test_stored_weight_hierarchy_matches_oracle(ctx):
+    """Operator-dependent weights on level 0: Galerkin operators, V-cycle and PCG agree with
+    the oracle built on the same weights."""
+    from oracle import cycle, hierarchy, krylov
+    from oracle.learned import opdep_weights
+    p = _hc()
+    for smoother in ("jacobi", "chebyshev"):
+        dp, lay, h = _setup(ctx, p, 3, smoother)
+        n_r = lay.sizes()["n_regional"]
+        wr = torch.empty(3 * n_r, dtype=torch.float64, device="cuda")
+        h.opdep_weights(0, wr)
+        h.set_transfer_weights(0, wr)
+        h.setup_numeric()
+        w0 = opdep_weights(p.A, p.global_dims)
+        levels = hierarchy.build(p, 3, weights=lambda l, lev: w0 if l == 0 else None)
+        mg = cycle.RegionalMG(levels, _opts(smoother))
+        for l, lev in enumerate(levels):
+            n_l, _, kind = h.level_sizes(l)
+            coef = torch.empty(kind * n_l, dtype=torch.float64, device="cuda")
+            h.level_export(l, coeffs=coef)
+            M = stencils_to_matrix(lev.layout.region_dims, coef.cpu().numpy(), kind)
+            assert matrix_rel_diff(M, lev.Ar) <= 1e-12, (smoother, l)
+        L0 = levels[0].layout
+        z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+        h.vcycle(dp.b, z)
+        expect = L0.average_to_composite(mg.precondition(L0.to_regional(p.b)))
+        assert rel_max(z.cpu().numpy(), expect) <= 1e-10
+        x_or, it_or, _ = krylov.pcg(p.A, p.b, krylov.regional_preconditioner(mg), rtol=1e-10)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        res = h.pcg(dp.b, x, rtol=1e-10, maxit=200)
+        assert res["iterations"] == it_or
+        # restoring linear interpolation gives back the plain hierarchy
+        h.set_transfer_weights(0, None)
+        h.setup_numeric()
+        plain = cycle.RegionalMG(hierarchy.build(p, 3), _opts(smoother))
+        h.vcycle(dp.b, z)
+        expect = L0.average_to_composite(plain.precondition(L0.to_regional(p.b)))
+        assert rel_max(z.cpu().numpy(), expect) <= 1e-10
+
+
+def test_convergence_factor_matches_oracle(ctx):
+    from oracle import cycle, hierarchy
+    from oracle.rng import uniform_pm1
+    p = _hc()
+    dp, lay, h = _setup(ctx, p, 3, "chebyshev")
+    fac = h.convergence_factor(5, 11)
+    levels = hierarchy.build(p, 3)
+    mg = cycle.RegionalMG(levels, _opts("chebyshev"))
+    L0 = levels[0].layout
+    e = uniform_pm1(11, np.arange(p.n_nodes))
+    e[p.dirichlet.astype(bool)] = 0.0
+    er = L0.to_regional(e)
+    A = lambda v: L0.interface_sum(levels[0].Ar @ v)
+    e0 = L0.dot(er, A(er))
+    for _ in range(5):
+        er = er - mg.precondition(A(er))
+    e5 = L0.dot(er, A(er))
+    assert fac == pytest.approx((e5 / e0) ** (0.5 / 5), rel=1e-8)
+
+
+def test_features_identical_on_copies(ctx):
+    p = _hc()
+    dp, lay, h = _setup(ctx, p)
+    n_r = lay.sizes()["n_regional"]
+    feats = torch.empty((n_r, 32), dtype=torch.float32, device="cuda")
+    h.mlp_features(0, feats)
+    f = feats.cpu().numpy()
+    g = p.region_gids
+    order = np.argsort(g, kind="stable")
+    gs = g[order]
+    same = gs[1:] == gs[:-1]
+    assert same.any()
+    assert np.array_equal(f[order][1:][same], f[order][:-1][same])
+    assert np.isfinite(f).all()
+
+
+def test_mlp_forward_and_gradient_match_oracle(ctx):
+    from oracle import learned as Lo
+    from paper_2103_11962_gb300 import learned, rmg
+    p = _hc()
+    dp, lay, h = _setup(ctx, p)
+    n_r = lay.sizes()["n_regional"]
+    feats = torch.empty((n_r, 32), dtype=torch.float32, device="cuda")
+    h.mlp_features(0, feats)
+    rng = np.random.default_rng(5)
+    sel = rng.choice(n_r, 1000, replace=False)
+    X = feats[torch.from_numpy(sel).cuda()].contiguous()
+    Y = torch.from_numpy(rng.uniform(0, 1, (1000, 3)).astype(np.float32)).cuda()
+    M = torch.from_numpy((rng.uniform(0, 1, (1000, 3)) > 0.25).astype(np.float32)).cuda()
+    params = learned.init_params(3)
+    net = rmg.MLP(ctx, params)
+    out = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
+    net.forward(X, out)
+    O_or, _ = Lo.forward(params.astype(np.float64), X.cpu().numpy().astype(np.float64))
+    assert np.abs(out.cpu().numpy() - O_or).max() <= 2e-3
+    loss, g = net.gradient(X, Y, M)
+    L_or, g_or = Lo.loss_and_grad(params.astype(np.float64), X.cpu().numpy().astype(np.float64),
+                                  Y.cpu().numpy().astype(np.float64),
+                                  M.cpu().numpy().astype(np.float64))
+    assert loss == pytest.approx(L_or, rel=1e-3)
+    assert np.linalg.norm(g - g_or) <= 1e-3 * np.linalg.norm(g_or)
+
+
+def test_trained_network_against_plain_method(ctx):
+    """Train on operators labelled by the plain method, then compare on a held-out
+    high-contrast operator: the accepted prolongator is never worse than linear, and the
+    network's prediction is reported against both the plain and the operator-dependent one."""
+    from paper_2103_11962_gb300 import learned
+    mk = lambda s: W.highcontrast3d_7pt(region_grid=(2, 2, 2), choices=(10,), seed=1000 + s)
+    F, Y, M, factors = learned.training_set(ctx, range(12), mk)
+    assert F.shape[0] == Y.shape[0] == M.shape[0]
+    net, hist = learned.train(ctx, F, Y, M, steps=400, batch=4096, lr=3e-3)
+    assert np.isfinite(hist).all()
+    assert hist[-50:].mean() < hist[:10].mean()
+    p = W.highcontrast3d_7pt(region_grid=(3, 3, 2), choices=(10, 19), seed=77)
+    dp, lay, h = _setup(ctx, p, 3)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    plain = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+    res = learned.apply_learned(h, net, lay.sizes()["n_regional"])
+    x.zero_()
+    after = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+    print(f"plain {plain['iterations']} its (factor {res['factor_plain']:.3f}); learned factor "
+          f"{res['factor_learned']:.3f}, accepted {res['accepted']}; after: {after['iterations']} its")
+    assert after["converged"] and after["true_relres"] <= 1.5e-10
+    if res["accepted"]:
+        assert res["factor_learned"] <= res["factor_plain"]
+    else:
+        assert after["iterations"] == plain["iterations"]

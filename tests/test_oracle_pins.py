@@ -494,3 +494,97 @@ def test_jacobi_mg_contraction_band():
         res.append(np.linalg.norm(p.b - p.A @ lay.average_to_composite(u)))
     rates = np.array(res[1:]) / np.array(res[:-1])
     assert np.all(rates[2:] < 0.5)
+
+
+# ---------------------------------------------------------------------------- learned prolongator
+def test_stored_p_with_linear_weights_is_linear_p():
+    from oracle.transfer import stored_p
+    dims = (19, 10, 7)
+    n = int(np.prod(dims))
+    g = np.arange(n)
+    coord = [g % 19, (g // 19) % 10, g // 190]
+    wr = np.stack([(c % 3) / 3.0 for c in coord])
+    fm = np.zeros(n, bool); fm[::7] = True
+    cm = np.zeros(7 * 4 * 3, bool); cm[::5] = True
+    A = stored_p(dims, wr, fm, cm)
+    B = composite_p(dims, fm, cm)
+    assert abs(A - B).max() == 0.0
+
+
+def test_opdep_weights_constant_coefficient_is_linear():
+    from oracle.learned import opdep_weights
+    p = W.q1_laplace3d(region_grid=(1, 1, 1), n=10)     # not an M-matrix: linear fallback
+    p7 = W.diffusion3d_7pt(region_grid=(2, 1, 1), choices=(10,), seed=0, sigma=0.0)
+    for prob in (p, p7):
+        wr = opdep_weights(prob.A, prob.global_dims)
+        Nx, Ny, Nz = prob.global_dims
+        g = np.arange(prob.n_nodes)
+        coord = [g % Nx, (g // Nx) % Ny, g // (Nx * Ny)]
+        free = ~prob.dirichlet.astype(bool)
+        # away from the Dirichlet boundary every conductance on a line is equal
+        inner = free.copy()
+        for c, N in zip(coord, (Nx, Ny, Nz)):
+            inner &= (c >= 3) & (c <= N - 4)
+        for a in range(3):
+            r = coord[a] % 3
+            sel = inner & (r != 0)
+            assert np.allclose(wr[a][sel], r[sel] / 3.0, atol=1e-14)
+
+
+def test_opdep_weights_make_flux_continuous():
+    """With the series-resistance weights the interpolated values on a line between two
+    coarse nodes carry the same flux k_e (v_e+1 - v_e) across all three edges: the discrete
+    1D A-harmonic extension."""
+    from oracle.learned import opdep_weights
+    p = W.highcontrast3d_7pt(region_grid=(3, 2, 2), choices=(10,), seed=13)
+    wr = opdep_weights(p.A, p.global_dims)
+    Nx, Ny, Nz = p.global_dims
+    A = p.A.tocsr()
+    rng = np.random.default_rng(2)
+    checked = 0
+    for _ in range(400):
+        x, y, z = rng.integers(1, Nx - 1), rng.integers(1, Ny - 1), rng.integers(1, Nz - 1)
+        rem = x % 3
+        if rem == 0 or x - rem + 3 >= Nx:
+            continue
+        x0 = x - rem
+        nodes = [x0 + e + Nx * (y + Ny * z) for e in range(4)]
+        k = np.array([-A[nodes[e], nodes[e + 1]] for e in range(3)])
+        if np.any(k <= 0):
+            continue
+        v0, v3 = 0.3, 1.7
+        w1, w2 = wr[0][nodes[1]], wr[0][nodes[2]]
+        v = [v0, v0 + w1 * (v3 - v0), v0 + w2 * (v3 - v0), v3]
+        flux = [k[e] * (v[e + 1] - v[e]) for e in range(3)]
+        assert np.allclose(flux, flux[0], rtol=1e-12)
+        checked += 1
+    assert checked > 50
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import learned as Lm
+    rng = np.random.default_rng(0)
+    params = rng.standard_normal(Lm.NPARAMS) * 0.3
+    X = rng.standard_normal((40, Lm.NFEAT))
+    Y = rng.uniform(0, 1, (40, 3))
+    M = (rng.uniform(0, 1, (40, 3)) > 0.3).astype(float)
+    L0, g = Lm.loss_and_grad(params, X, Y, M, rounding=False)
+    idx = rng.choice(Lm.NPARAMS, 60, replace=False)
+    for i in idx:
+        e = np.zeros(Lm.NPARAMS); e[i] = 1e-6
+        lp, _ = Lm.loss_and_grad(params + e, X, Y, M, rounding=False)
+        lm, _ = Lm.loss_and_grad(params - e, X, Y, M, rounding=False)
+        fd = (lp - lm) / 2e-6
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9)
+
+
+def test_bf16_rounding_matches_definition():
+    from oracle.learned import bf16_round
+    # bfloat16 keeps 8 significand bits; ties go to even
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, -2.5, 3.0e-39])
+    out = bf16_round(vals)
+    assert out[0] == 1.0
+    assert out[1] == 1.0                     # tie between 1 and 1 + 2^-7: even (1.0)
+    assert out[2] == 1.0 + 2 ** -6          # tie between 1+2^-7 and 1+2^-6: even mantissa
+    assert out[3] == 1.0
+    assert out[4] == -2.5
