@@ -177,16 +177,19 @@ void rmg_hier_destroy(rmg_hier* hier);
  * from its right coarse neighbour along axis a (1 - wr from the left one); it is ignored along
  * axes where n sits on a coarse index. Co-located copies must carry identical weights and
  * interface nodes may only use interface coarse nodes (Lemma 2); weights computed from
- * composite data satisfy both. wr = NULL restores linear interpolation. Call
+ * composite data satisfy both. The entries of P are the FP32 products wz (wy wx) of the
+ * per-axis weights (1 - w for the left neighbour, also in FP32), in every precision of the
+ * cycle and in the Galerkin products. wr = NULL restores linear interpolation. Call
  * rmg_setup_numeric afterwards (it rebuilds the Galerkin products and, if the kind of
  * transfer changed, re-captures the V-cycle graph). Levels 0 .. levels-2.
  */
-rmg_status rmg_hier_set_transfer_weights(rmg_hier* hier, int level, const double* wr);
-/* Operator-dependent weights of a level (device double[3 * n_r], layout as above): along each
+rmg_status rmg_hier_set_transfer_weights(rmg_hier* hier, int level, const float* wr);
+/* Operator-dependent weights of a level (device float[3 * n_r], layout as above, computed in
+ * FP64 and rounded): along each
  * axis the fine nodes between two coarse nodes are weighted by the series resistances
  * 1/(-A_ij) of the three composite couplings on that line (the 1D A-harmonic extension,
  * linear for constant coefficients; linear where a coupling is not negative). */
-rmg_status rmg_hier_opdep_weights(rmg_hier* hier, int level, double* wr);
+rmg_status rmg_hier_opdep_weights(rmg_hier* hier, int level, float* wr);
 
 /*
  * Learned prolongator (no counterpart in the paper, which keeps linear interpolation and
@@ -218,10 +221,10 @@ rmg_status rmg_mlp_train(rmg_mlp* mlp, int n, const float* feats, const float* l
                          unsigned long long seed, float* loss_history);
 /* Features of every regional node of a hierarchy level (device float[n_r][32]). */
 rmg_status rmg_hier_mlp_features(rmg_hier* hier, int level, float* feats);
-/* Network inference on a level: per-axis weights (device double[3 * n_r]) for
+/* Network inference on a level: per-axis weights (device float[3 * n_r]) for
  * rmg_hier_set_transfer_weights (zero along axes where a node sits on a coarse index).
  * Synchronises. */
-rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, double* wr);
+rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, float* wr);
 
 /* Measured convergence of the V-cycle as a stationary solver: from a SplitMix64 random
  * error e (stream `seed`, zero at masked nodes), iterate e <- e - M^-1 A e `iters` times and

@@ -59,13 +59,16 @@ def stored_p(global_dims, wr, fine_mask, coarse_mask) -> sp.csr_matrix:
     """P with stored per-node weights (Table 4's "general grid transfers": the sparsity of 3:1
     linear interpolation with coefficients of choice).
 
-    ``wr`` is (3, n_fine): the weight fine node f takes from its right coarse neighbour along
-    axis a; the left neighbour gets 1 - wr; along an axis where f sits on a coarse index the
-    weight is 1. The row is the tensor product of the three axis weights.
+    ``wr`` is (3, n_fine), FP32: the weight fine node f takes from its right coarse neighbour
+    along axis a; the left neighbour gets 1 - wr; along an axis where f sits on a coarse index
+    the weight is 1. The row is the tensor product of the three axis weights, formed in FP32
+    as wz (wy wx) (the library's definition of a stored-weight P).
     """
     Nx, Ny, Nz = global_dims
     cNx, cNy, cNz = coarse_count(Nx), coarse_count(Ny), coarse_count(Nz)
     n = Nx * Ny * Nz
+    wr = np.asarray(wr, dtype=np.float32)
+    one = np.float32(1.0)
     g = np.arange(n)
     coord = [g % Nx, (g // Nx) % Ny, g // (Nx * Ny)]
     c0 = [c // 3 for c in coord]
@@ -76,18 +79,18 @@ def stored_p(global_dims, wr, fine_mask, coarse_mask) -> sp.csr_matrix:
             for sa in (0, 1):
                 side = (sa, sb, sc)
                 ok = np.ones(n, bool)
-                w = np.ones(n)
+                w = None
                 cc = []
                 for a in range(3):
                     if side[a]:
                         ok &= rem[a] != 0
-                        wa = np.where(rem[a] != 0, wr[a], 0.0)
+                        wa = np.where(rem[a] != 0, wr[a], np.float32(0.0)).astype(np.float32)
                     else:
-                        wa = np.where(rem[a] != 0, 1.0 - np.asarray(wr[a]), 1.0)
+                        wa = np.where(rem[a] != 0, one - wr[a], one).astype(np.float32)
                     cc.append(c0[a] + side[a])
-                    w = w * wa if a == 0 else wa * w
+                    w = wa if w is None else (wa * w).astype(np.float32)
                 col = cc[0] + cNx * (cc[1] + cNy * cc[2])
-                rows.append(g[ok]); cols.append(col[ok]); vals.append(w[ok])
+                rows.append(g[ok]); cols.append(col[ok]); vals.append(w[ok].astype(np.float64))
     P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(n, cNx * cNy * cNz))
     keep_rows = sp.diags((~np.asarray(fine_mask, bool)).astype(float))

@@ -251,12 +251,12 @@ rmg_status rmg_hier_level_export(rmg_hier* hh, int level, double* coeffs, double
   });
 }
 
-rmg_status rmg_hier_set_transfer_weights(rmg_hier* hh, int level, const double* wr) {
+rmg_status rmg_hier_set_transfer_weights(rmg_hier* hh, int level, const float* wr) {
   if (!hh) return RMG_ERR_ARG;
   return guarded(hh->h.layout->ctx, [&] { set_transfer_weights(hh->h, level, wr); });
 }
 
-rmg_status rmg_hier_opdep_weights(rmg_hier* hh, int level, double* wr) {
+rmg_status rmg_hier_opdep_weights(rmg_hier* hh, int level, float* wr) {
   if (!hh) return RMG_ERR_ARG;
   return guarded(hh->h.layout->ctx, [&] {
     RMG_REQUIRE(wr, RMG_ERR_ARG, "wr is NULL");

@@ -215,7 +215,7 @@ struct Exec {
   // [[Psi Psi^T]]^-1 scaling of the restriction
   void residual(int l) { stencil(l, cur[l], EpiResidScaled<VT>{V(l).b.get(), V(l).r.get()}); }
 
-  const VT* pw(int l) const;
+  const float* pw(int l) const { return h.lv[l]->pw.get(); }
 
   void restrict_to(int l) {
     const Level& F = *h.lv[l];
@@ -310,9 +310,6 @@ struct Exec {
   }
 };
 
-template <> const double* Exec<double, double>::pw(int l) const { return h.lv[l]->pw.get(); }
-template <> const float* Exec<float, float>::pw(int l) const { return h.lv[l]->pw32.get(); }
-template <> const float* Exec<float, __nv_bfloat16>::pw(int l) const { return h.lv[l]->pw32.get(); }
 template <> LevelVecs<double>& Exec<double, double>::V(int l) { return h.v64[l]; }
 template <> const double* Exec<double, double>::coef(int l) const { return h.lv[l]->coef.get(); }
 template <> const double* Exec<double, double>::dinv(int l) const { return h.lv[l]->dinv.get(); }
@@ -521,7 +518,7 @@ static void galerkin(Hier& h, const Level& F, Level& C) {
 // Stored transfer weights for level -> level+1 (NULL restores linear interpolation). The
 // numeric setup must run afterwards; it re-captures the V-cycle graph when the kind of
 // transfer of a level changed.
-void set_transfer_weights(Hier& h, int level, const double* wr) {
+void set_transfer_weights(Hier& h, int level, const float* wr) {
   RMG_REQUIRE(level >= 0 && level + 1 < h.levels(), RMG_ERR_ARG,
               "transfer weights exist for levels 0 .. levels-2");
   Level& L = *h.lv[level];
@@ -531,12 +528,11 @@ void set_transfer_weights(Hier& h, int level, const double* wr) {
   }
   L.pw.ensure((size_t)3 * L.n_r);
   RMG_CUDA(cudaMemcpyAsync(L.pw.get(), wr, L.pw.bytes(), cudaMemcpyDeviceToDevice, h.c->stream));
-  if (h.mixed()) L.pw32.ensure((size_t)3 * L.n_r);
   L.stored_p = true;
 }
 
 // Operator-dependent (series-resistance) weights of a level from its current operator.
-void opdep_weights(Hier& h, int level, double* wr) {
+void opdep_weights(Hier& h, int level, float* wr) {
   RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
   Level& L = *h.lv[level];
   Ctx& c = *h.c;
@@ -647,11 +643,6 @@ static void make_low_precision(Hier& h) {
     RMG_LAUNCHED();
     k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.n_r, L.dinv.get(), L.dinv32.get());
     RMG_LAUNCHED();
-    if (L.stored_p) {
-      L.pw32.ensure((size_t)3 * L.n_r);
-      k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)3 * L.n_r, L.pw.get(), L.pw32.get());
-      RMG_LAUNCHED();
-    }
   }
 }
 

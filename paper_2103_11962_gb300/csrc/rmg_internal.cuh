@@ -180,10 +180,10 @@ struct Level {
   DBuf<__nv_bfloat16> coef16;
   DBuf<float> dinv32;
   // stored transfer weights to the next coarser level (linear 3:1 when not stored):
-  // pw[a * n_r + n] = weight of the right coarse neighbour along axis a
+  // pw[a * n_r + n] = weight of the right coarse neighbour along axis a (FP32; the entries of
+  // P are the FP32 products wz (wy wx) in every precision)
   bool stored_p = false;
-  DBuf<double> pw;
-  DBuf<float> pw32;
+  DBuf<float> pw;
 
   Grid grid() const { return Grid{regions.get(), tiles.get(), (int)htiles.size(), nreg, n_r}; }
 };

@@ -308,7 +308,7 @@ __device__ __forceinline__ T pw_seen_from_coarse(const W* __restrict__ wr, int n
 
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kTile)
-k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const VT* __restrict__ wr,
+k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const float* __restrict__ wr,
              const VT* __restrict__ rs, const uint8_t* __restrict__ cmask,
              const uint8_t* __restrict__ cmult, VT* __restrict__ w, VT* __restrict__ yc) {
   RMG_FOR_NODES(Gc)
@@ -328,10 +328,10 @@ k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const VT
             const int fx = 3 * I + a;
             if (fx < 0 || fx >= F.nx) continue;
             const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-            const VT wz = DIM == 3 ? pw_seen_from_coarse<VT>(wr, fn_r, f, 2, c) : VT(1);
-            const VT wgt = wz * (pw_seen_from_coarse<VT>(wr, fn_r, f, 1, b) *
-                                 pw_seen_from_coarse<VT>(wr, fn_r, f, 0, a));
-            acc = fma(wgt, rs[f], acc);
+            const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
+            const float wgt = wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
+                                    pw_seen_from_coarse<float>(wr, fn_r, f, 0, a));
+            acc = fma(VT(wgt), rs[f], acc);
           }
         }
       }
@@ -342,7 +342,7 @@ k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const VT
 
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kTile)
-k_prolong_w(Grid Gf, const RegionDev* __restrict__ cregions, const VT* __restrict__ wr,
+k_prolong_w(Grid Gf, const RegionDev* __restrict__ cregions, const float* __restrict__ wr,
             const uint8_t* __restrict__ fmask, const VT* __restrict__ ubar, VT* __restrict__ u) {
   RMG_FOR_NODES(Gf)
     if (fmask[n]) continue;
@@ -351,11 +351,11 @@ k_prolong_w(Grid Gf, const RegionDev* __restrict__ cregions, const VT* __restric
     const RegionDev C = cregions[tile_.region];
     const int co[3] = {i / 3, j / 3, DIM == 3 ? l / 3 : 0};
     const int rm[3] = {i - 3 * co[0], j - 3 * co[1], DIM == 3 ? l - 3 * co[2] : 0};
-    VT w0[3], w1[3];
+    float w0[3], w1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const VT r = rm[a] ? VT(wr[(size_t)a * Gf.n_r + n]) : VT(0);
-      w0[a] = VT(1) - r;
+      const float r = rm[a] ? wr[(size_t)a * Gf.n_r + n] : 0.f;
+      w0[a] = 1.f - r;
       w1[a] = r;
     }
     const int base = C.off + co[0] + C.nx * (co[1] + C.ny * co[2]);
@@ -363,8 +363,8 @@ k_prolong_w(Grid Gf, const RegionDev* __restrict__ cregions, const VT* __restric
     for (int c = 0; c < (rm[2] ? 2 : 1); ++c)
       for (int b = 0; b < (rm[1] ? 2 : 1); ++b)
         for (int a = 0; a < (rm[0] ? 2 : 1); ++a) {
-          const VT wgt = (c ? w1[2] : w0[2]) * ((b ? w1[1] : w0[1]) * (a ? w1[0] : w0[0]));
-          acc = fma(wgt, ubar[base + a + C.nx * (b + C.ny * c)], acc);
+          const float wgt = (c ? w1[2] : w0[2]) * ((b ? w1[1] : w0[1]) * (a ? w1[0] : w0[0]));
+          acc = fma(VT(wgt), ubar[base + a + C.nx * (b + C.ny * c)], acc);
         }
     u[n] = u[n] + acc;
   RMG_END_FOR_NODES

@@ -324,10 +324,10 @@ k_features(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ 
 
 // Predicted weights -> per-axis interpolation weights (0 along inactive axes).
 __global__ void k_weights_from_out(int n_r, const float* __restrict__ feats,
-                                   const float* __restrict__ out, double* __restrict__ wr) {
+                                   const float* __restrict__ out, float* __restrict__ wr) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < n_r; n += gridDim.x * blockDim.x)
     for (int a = 0; a < 3; ++a)
-      wr[(size_t)a * n_r + n] = feats[(size_t)n * NF + 9 * a + 8] > 0.5f ? (double)out[n * 3 + a] : 0.0;
+      wr[(size_t)a * n_r + n] = feats[(size_t)n * NF + 9 * a + 8] > 0.5f ? out[n * 3 + a] : 0.f;
 }
 
 size_t mlp_smem() { return sizeof(MlpSmem); }
@@ -486,7 +486,7 @@ rmg_status rmg_hier_mlp_features(rmg_hier* hh, int level, float* feats) {
   });
 }
 
-rmg_status rmg_hier_mlp_weights(rmg_hier* hh, int level, rmg_mlp* net, double* wr) {
+rmg_status rmg_hier_mlp_weights(rmg_hier* hh, int level, rmg_mlp* net, float* wr) {
   if (!hh || !net) return RMG_ERR_ARG;
   rmg_status st = RMG_OK;
   Hier& h = hh->h;

@@ -191,7 +191,7 @@ k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ 
 template <int FK, int DIM>
 __global__ void __launch_bounds__(kTile)
 k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fcoef,
-       const double* __restrict__ wr, const uint8_t* __restrict__ fmask,
+       const float* __restrict__ wr, const uint8_t* __restrict__ fmask,
        const uint8_t* __restrict__ cmask, double* __restrict__ ap) {
   using FS = Sten<FK>;
   constexpr int NO = DIM == 3 ? 27 : 9;
@@ -217,17 +217,17 @@ k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ 
         const int x0 = gx / 3, rx = gx - 3 * x0;
         const int y0 = gy / 3, ry = gy - 3 * y0;
         const int z0 = DIM == 3 ? gz / 3 : 0, rz = DIM == 3 ? gz - 3 * z0 : 0;
-        const double wx = rx ? wr[f2] : 0.0;
-        const double wy = ry ? wr[(size_t)Gf.n_r + f2] : 0.0;
-        const double wz = rz ? wr[(size_t)2 * Gf.n_r + f2] : 0.0;
+        const float wx = rx ? wr[f2] : 0.f;
+        const float wy = ry ? wr[(size_t)Gf.n_r + f2] : 0.f;
+        const float wz = rz ? wr[(size_t)2 * Gf.n_r + f2] : 0.f;
         for (int c = 0; c < (rz ? 2 : 1); ++c)
           for (int b = 0; b < (ry ? 2 : 1); ++b)
             for (int a = 0; a < (rx ? 2 : 1); ++a) {
               const int X = x0 + a, Y = y0 + b, Z = z0 + c;
               if (cmask[C.off + X + C.nx * (Y + C.ny * Z)]) continue;
-              const double wgt = (c ? wz : 1.0 - wz) * ((b ? wy : 1.0 - wy) * (a ? wx : 1.0 - wx));
+              const float wgt = (c ? wz : 1.f - wz) * ((b ? wy : 1.f - wy) * (a ? wx : 1.f - wx));
               const int o = (X - cx0) + 3 * (Y - cy0) + 9 * (Z - cz0);
-              acc[o][tid] = fma(v, wgt, acc[o][tid]);
+              acc[o][tid] = fma(v, (double)wgt, acc[o][tid]);
             }
       }
     }
@@ -239,7 +239,7 @@ k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ 
 template <int CK, int DIM>
 __global__ void __launch_bounds__(kTile)
 k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
-         const double* __restrict__ wr, const uint8_t* __restrict__ cmask,
+         const float* __restrict__ wr, const uint8_t* __restrict__ cmask,
          const uint8_t* __restrict__ cmult, double* __restrict__ ccoef) {
   using CS = Sten<CK>;
   RMG_FOR_NODES(Gc)
@@ -262,9 +262,9 @@ k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict_
             const int fx = 3 * I + a;
             if (fx < 0 || fx >= F.nx) continue;
             const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-            const double wz = DIM == 3 ? pw_seen_from_coarse<double>(wr, fn_r, f, 2, c) : 1.0;
-            const double wf = wz * (pw_seen_from_coarse<double>(wr, fn_r, f, 1, b) *
-                                    pw_seen_from_coarse<double>(wr, fn_r, f, 0, a));
+            const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
+            const double wf = (double)(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
+                                             pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
             if (wf == 0.0) continue;
             const int bx = a <= 0 ? 1 : 0, by = b <= 0 ? 1 : 0, bz = DIM == 3 ? (c <= 0 ? 1 : 0) : 0;
 #pragma unroll
@@ -299,7 +299,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kTile)
 k_opdep(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ mult,
         const int* __restrict__ gid, const int* __restrict__ cgrp, const int* __restrict__ gptr,
-        const int* __restrict__ gslot, double* __restrict__ wr) {
+        const int* __restrict__ gslot, float* __restrict__ wr) {
   constexpr int DIM = Sten<KIND>::DIM;
   RMG_FOR_NODES(G)
     int x[3];
@@ -328,7 +328,7 @@ k_opdep(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ mul
           w = rem / 3.0;
         }
       }
-      wr[(size_t)a * G.n_r + n] = w;
+      wr[(size_t)a * G.n_r + n] = (float)w;
     }
   RMG_END_FOR_NODES
 }

@@ -63,13 +63,13 @@ def label_operator(ctx, problem, levels=2, iters=6, seed=7, device="cuda:0"):
     feats = torch.empty((n_r, NFEAT), dtype=torch.float32, device=device)
     h.mlp_features(0, feats)
     f_lin = h.convergence_factor(iters, seed)
-    wr = torch.empty(3 * n_r, dtype=torch.float64, device=device)
+    wr = torch.empty(3 * n_r, dtype=torch.float32, device=device)
     h.opdep_weights(0, wr)
     h.set_transfer_weights(0, wr)
     h.setup_numeric()
     f_op = h.convergence_factor(iters, seed)
     if f_op < f_lin:
-        labels = wr.view(3, n_r).t().to(torch.float32).contiguous()
+        labels = wr.view(3, n_r).t().contiguous()
     else:
         labels = feats[:, REMFRAC].contiguous()
     interior = (dp.dirichlet[dp.gids] == 0).to(torch.float32)
@@ -102,7 +102,7 @@ def apply_learned(h, net, n_regional, levels=(0,), iters=6, seed=7, device="cuda
     f_plain = h.convergence_factor(iters, seed)
     for l in levels:
         n_l = h.level_sizes(l)[0]
-        wr = torch.empty(3 * n_l, dtype=torch.float64, device=device)
+        wr = torch.empty(3 * n_l, dtype=torch.float32, device=device)
         h.mlp_weights(l, net, wr)
         h.set_transfer_weights(l, wr)
     h.setup_numeric()

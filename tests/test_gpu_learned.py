@@ -43,12 +43,13 @@ def test_opdep_weights_match_oracle(ctx):
     for p in (_hc(), W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=5)):
         dp, lay, h = _setup(ctx, p)
         n_r = lay.sizes()["n_regional"]
-        wr = torch.empty(3 * n_r, dtype=torch.float64, device="cuda")
+        wr = torch.empty(3 * n_r, dtype=torch.float32, device="cuda")
         h.opdep_weights(0, wr)
-        got = wr.view(3, n_r).cpu().numpy()
+        got = wr.view(3, n_r).cpu().numpy().astype(np.float64)
         expect = opdep_weights(p.A, p.global_dims)[:, p.region_gids]
         free = ~p.dirichlet.astype(bool)[p.region_gids]
-        assert np.abs(got[:, free] - expect[:, free]).max() <= 1e-12
+        # FP64 weights rounded to FP32 (unit roundoff 6e-8 on values in [0, 1])
+        assert np.abs(got[:, free] - expect[:, free]).max() <= 1.2e-7
 
 
 def test_stored_weight_hierarchy_matches_oracle(ctx):
@@ -60,11 +61,14 @@ def test_stored_weight_hierarchy_matches_oracle(ctx):
     for smoother in ("jacobi", "chebyshev"):
         dp, lay, h = _setup(ctx, p, 3, smoother)
         n_r = lay.sizes()["n_regional"]
-        wr = torch.empty(3 * n_r, dtype=torch.float64, device="cuda")
+        wr = torch.empty(3 * n_r, dtype=torch.float32, device="cuda")
         h.opdep_weights(0, wr)
         h.set_transfer_weights(0, wr)
         h.setup_numeric()
-        w0 = opdep_weights(p.A, p.global_dims)
+        # the stored weights are an input of the transfer: hand the same FP32 values to the
+        # oracle (composite id -> weights; co-located copies hold identical values)
+        w0 = np.zeros((3, p.n_nodes), dtype=np.float32)
+        w0[:, p.region_gids] = wr.view(3, n_r).cpu().numpy()
         levels = hierarchy.build(p, 3, weights=lambda l, lev: w0 if l == 0 else None)
         mg = cycle.RegionalMG(levels, _opts(smoother))
         for l, lev in enumerate(levels):
@@ -155,27 +159,35 @@ def test_mlp_forward_and_gradient_match_oracle(ctx):
 
 
 def test_trained_network_against_plain_method(ctx):
-    """Train on operators labelled by the plain method, then compare on a held-out
-    high-contrast operator: the accepted prolongator is never worse than linear, and the
-    network's prediction is reported against both the plain and the operator-dependent one."""
+    """Train on small log-normal-coefficient operators labelled by the plain method, then
+    compare on held-out operators: a C2-shaped one (the network must not lose against linear
+    interpolation and its gain is reported) and a high-contrast one whose jumps sit on coarse
+    grid planes (linear interpolation is already the operator-dependent one there; the
+    accept rule must keep the plain prolongator or an equivalent one)."""
     from paper_2103_11962_gb300 import learned
-    mk = lambda s: W.highcontrast3d_7pt(region_grid=(2, 2, 2), choices=(10,), seed=1000 + s)
-    F, Y, M, factors = learned.training_set(ctx, range(12), mk)
+    mk = lambda s: W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=2000 + s)
+    F, Y, M, factors = learned.training_set(ctx, range(16), mk)
     assert F.shape[0] == Y.shape[0] == M.shape[0]
-    net, hist = learned.train(ctx, F, Y, M, steps=400, batch=4096, lr=3e-3)
+    assert np.mean(factors[:, 1] < factors[:, 0]) > 0.5       # the teacher usually wins
+    net, hist = learned.train(ctx, F, Y, M, steps=600, batch=8192, lr=2e-3)
     assert np.isfinite(hist).all()
-    assert hist[-50:].mean() < hist[:10].mean()
-    p = W.highcontrast3d_7pt(region_grid=(3, 3, 2), choices=(10, 19), seed=77)
-    dp, lay, h = _setup(ctx, p, 3)
-    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
-    plain = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
-    res = learned.apply_learned(h, net, lay.sizes()["n_regional"])
-    x.zero_()
-    after = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
-    print(f"plain {plain['iterations']} its (factor {res['factor_plain']:.3f}); learned factor "
-          f"{res['factor_learned']:.3f}, accepted {res['accepted']}; after: {after['iterations']} its")
-    assert after["converged"] and after["true_relres"] <= 1.5e-10
-    if res["accepted"]:
-        assert res["factor_learned"] <= res["factor_plain"]
-    else:
-        assert after["iterations"] == plain["iterations"]
+    assert hist[-50:].mean() < 0.5 * hist[:10].mean()
+    for p in (W.diffusion3d_7pt(region_grid=(3, 3, 2), choices=(10, 19, 28), seed=77),
+              W.highcontrast3d_7pt(region_grid=(3, 3, 2), choices=(10, 19), seed=77)):
+        dp, lay, h = _setup(ctx, p, 3)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        plain = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+        res = learned.apply_learned(h, net, lay.sizes()["n_regional"])
+        x.zero_()
+        after = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+        print(f"{p.name}: plain {plain['iterations']} its (factor {res['factor_plain']:.4f}); "
+              f"learned factor {res['factor_learned']:.4f}, accepted {res['accepted']}; "
+              f"after: {after['iterations']} its")
+        assert after["converged"] and after["true_relres"] <= 1.5e-10
+        if res["accepted"]:
+            assert res["factor_learned"] <= res["factor_plain"]
+            assert after["iterations"] <= plain["iterations"] + 1
+        else:
+            assert after["iterations"] == plain["iterations"]
+        if p.name == "diffusion3d_7pt":
+            assert res["factor_learned"] < res["factor_plain"] * 1.01

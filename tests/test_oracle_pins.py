@@ -508,7 +508,9 @@ def test_stored_p_with_linear_weights_is_linear_p():
     cm = np.zeros(7 * 4 * 3, bool); cm[::5] = True
     A = stored_p(dims, wr, fm, cm)
     B = composite_p(dims, fm, cm)
-    assert abs(A - B).max() == 0.0
+    # same sparsity; entries equal up to the FP32 rounding of the stored weights
+    assert (A != 0).sum() == (B != 0).sum()
+    assert abs(A - B).max() <= 2e-7
 
 
 def test_opdep_weights_constant_coefficient_is_linear():
