@@ -45,10 +45,42 @@ WORKLOADS = {
                                 "per-element kappa (sigma 1), Chebyshev degree 3, 4 levels"),
     "c2_quarter": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
                        desc="C2-shaped 3D 7-point diffusion on 4x4x2 regions (profiling size)"),
+    "c4_highcontrast3d": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                              desc="3D 7-point diffusion, 7x7x7 regions with per-axis node counts "
+                                   "from {28,55,82} (seed 3), kappa constant per region, "
+                                   "log-uniform in [1e-3, 1e3]"),
     "c1_poisson2d": dict(levels=4, smoother="jacobi", nu1=2, nu2=2, omega=0.67,
                          desc="2D Poisson 5-point, 2x2 regions of 82x82, Jacobi 0.67, nu 2/2, "
                               "4 levels"),
 }
+
+
+def training_family(workload):
+    """Seeded small operators the learned prolongator is trained on (same PDE family)."""
+    import workloads as W
+    if workload.startswith("c4"):
+        return lambda s: W.highcontrast3d_7pt(region_grid=(2, 2, 2), choices=(10,), seed=1000 + s)
+    return lambda s: W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=2000 + s)
+
+
+def profiled_traffic(prec):
+    """DRAM bytes per regional node of the timed sweep from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_stencil7_cheb_c2quarter.md")
+    if not os.path.exists(prof):
+        return None
+    h = hashlib.sha256()
+    for f in ("rmg_internal.cuh", "rmg_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2103_11962_gb300", "csrc", f), "rb").read())
+    text = open(prof).read()
+    if f"kernel_source_sha256_16: {h.hexdigest()[:16]}" not in text:
+        return None
+    key = {"fp64": "fp64", "fp32": "fp32"}.get(prec)
+    for line in text.splitlines():
+        if key and line.startswith(f"{key}_dram_bytes_per_node:"):
+            return float(line.split(":")[1])
+    return None
 
 
 def peaks():
@@ -174,6 +206,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-operators", type=int, default=40)
     ap.add_argument("--json-out", default=None, help="also write the JSON line to this file")
     args = ap.parse_args()
 
@@ -203,6 +237,8 @@ def main():
 
     if args.workload == "c2_quarter":
         p = W.diffusion3d_7pt(region_grid=(4, 4, 2), choices=(28, 55, 82), seed=1)
+    elif args.workload == "c4_highcontrast3d":
+        p = W.config("c4_highcontrast3d")
     else:
         p = W.config(args.workload)
     dp = upload(p, dev)
@@ -311,8 +347,12 @@ def main():
         else:
             roofline = dict(bound="hbm", achieved=round(gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
                             frac=round(hbm_frac, 4), peak_src=pk["src"])
+        tpn = profiled_traffic(prec)
         roofline.update(kernel=f"k_stencil<{p.stencil}, EpiCheb> level 0 ({prec})",
-                        traffic=None, ms_per_launch=round(kern_ms, 4),
+                        traffic=(round(tpn * n_r0) if tpn else None),
+                        traffic_src=("ncu dram__bytes per node (profiles/k_stencil7_cheb_c2quarter.md)"
+                                     " x regional nodes" if tpn else None),
+                        ms_per_launch=round(kern_ms, 4),
                         launches_timed=probe_n, bytes_per_launch=bytes_launch,
                         flops_per_launch=flops_launch)
 
@@ -360,9 +400,57 @@ def main():
                              pcg_iterations=im["iterations"], true_relres=im["true_relres"],
                              kernel_ms=km,
                              kernel_hbm_frac=(bl / (km / 1e3) / 1e9 / pk["hbm_gbs"]) if bl and km else None,
+                             kernel_traffic=(round(profiled_traffic(mp) * n_r0)
+                                             if profiled_traffic(mp) else None),
                              speedup_vs_fp64=ms_step / (msm / args.steps))
             hm.close()
         out["mixed"] = mixed
+
+    # learned prolongator: trained offline (outside the timed region) on small operators of the
+    # same family labelled by the plain method; inside every timed step the network predicts
+    # the level-0 weights from the new operator before the numeric setup
+    if not args.no_learned and p.stencil == 7:
+        from paper_2103_11962_gb300 import learned
+        t0 = time.perf_counter()
+        F, Y, M, factors = learned.training_set(ctx, range(args.train_operators),
+                                                training_family(args.workload), device=dev)
+        t1 = time.perf_counter()
+        net, hist = learned.train(ctx, F, Y, M, steps=1500, batch=16384, lr=2e-3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        wr = torch.empty(3 * p.n_regional_nodes, dtype=torch.float32, device=dev)
+
+        def lstep(h):
+            lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+            h.mlp_weights(0, net, wr)
+            h.set_transfer_weights(0, wr)
+            h.setup_numeric()
+            x.zero_()
+            return h.pcg(dp.b, x, rtol=RTOL, maxit=500, history=False)
+
+        lres = {"train_operators": args.train_operators, "samples": int(F.shape[0]),
+                "teacher_better_fraction": float(np.mean(factors[:, 1] < factors[:, 0])),
+                "label_s": t1 - t0, "train_s": t2 - t1, "loss_first": float(hist[0]),
+                "loss_last": float(hist[-1])}
+        del F, Y, M
+        for tag, prec in (("fp64", args.precision), ("fp32", "fp32")):
+            hl = hier if tag == "fp64" else rmg.Hierarchy(lay, options(prec))
+            acc = learned.apply_learned(hl, net, p.n_regional_nodes, device=dev)
+            entry = dict(acc)
+            if acc["accepted"]:
+                msl, infl, _, _ = timed(hl, args.steps, args.warmup, e2e=lstep)
+                il = infl[-1]
+                entry.update(ms_per_step=msl / args.steps, pcg_iterations=il["iterations"],
+                             true_relres=il["true_relres"],
+                             value=p.n_unknowns * il["vcycles"] * args.steps * world / (msl / 1e3),
+                             speedup_vs_fp64=ms_step / (msl / args.steps))
+                hl.set_transfer_weights(0, None)
+                hl.setup_numeric()
+            lres[tag] = entry
+            if hl is not hier:
+                hl.close()
+        out["learned"] = lres
+        net.close()
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs (composite
     # CSR + right-hand side) from pinned memory, the step, D2H of the solution

@@ -223,7 +223,7 @@ rmg_status rmg_mlp_train(rmg_mlp* mlp, int n, const float* feats, const float* l
 rmg_status rmg_hier_mlp_features(rmg_hier* hier, int level, float* feats);
 /* Network inference on a level: per-axis weights (device float[3 * n_r]) for
  * rmg_hier_set_transfer_weights (zero along axes where a node sits on a coarse index).
- * Synchronises. */
+ * Uses scratch kept by the hierarchy (allocated on the first call). */
 rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, float* wr);
 
 /* Measured convergence of the V-cycle as a stationary solver: from a SplitMix64 random

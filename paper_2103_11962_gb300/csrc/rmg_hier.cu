@@ -167,10 +167,13 @@ struct Exec {
 
   int elementwise_grid(int n) const { return persistent_grid(c(), (n + 255) / 256); }
 
+  // Chebyshev coefficients of level l, step k, in the cycle's precision
+  const VT* c1(int l, int k) const;
+  const VT* c2(int l, int k) const;
+
   void cheb_step(int l, int k, bool probe_it = false) {   // k >= 1
     probe = probe_it;
-    EpiCheb<VT> e{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c1[l][k], &sc()->cheb_c2[l][k],
-                  V(l).d.get(), oth[l]};
+    EpiCheb<VT> e{cur[l], V(l).b.get(), dinv(l), c1(l, k), c2(l, k), V(l).d.get(), oth[l]};
     stencil(l, cur[l], e);
     flip(l);
   }
@@ -196,13 +199,12 @@ struct Exec {
       for (int a = 0; a < nu; ++a) {
         if (a == 0 && from_zero) {
           k_cheb0_zero<VT><<<elementwise_grid(n), 256, 0, st>>>(n, V(l).b.get(), dinv(l),
-                                                                &sc()->cheb_c2[l][0],
-                                                                V(l).d.get(), oth[l]);
+                                                                c2(l, 0), V(l).d.get(), oth[l]);
           RMG_LAUNCHED();
           ++launches;
         } else {
           probe = probe_it && a == 0 && h.o.cheb_degree == 1;
-          stencil(l, cur[l], EpiCheb0<VT>{cur[l], V(l).b.get(), dinv(l), &sc()->cheb_c2[l][0],
+          stencil(l, cur[l], EpiCheb0<VT>{cur[l], V(l).b.get(), dinv(l), c2(l, 0),
                                           V(l).d.get(), oth[l]});
         }
         flip(l);
@@ -215,14 +217,14 @@ struct Exec {
   // [[Psi Psi^T]]^-1 scaling of the restriction
   void residual(int l) { stencil(l, cur[l], EpiResidScaled<VT>{V(l).b.get(), V(l).r.get()}); }
 
-  const float* pw(int l) const { return h.lv[l]->pw.get(); }
+  const float* pw(int l) const { return h.pw[l].get(); }
 
   void restrict_to(int l) {
     const Level& F = *h.lv[l];
     const Level& C = *h.lv[l + 1];
     const Grid Gc = C.grid();
     const int gb = persistent_grid(c(), Gc.ntiles);
-    if (F.stored_p) {
+    if (h.stored[l]) {
       if (F.dim == 3)
         k_restrict_w<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), F.n_r, pw(l), V(l).r.get(),
                                                   C.mask.get(), C.mult.get(), V(l + 1).b.get(),
@@ -252,7 +254,7 @@ struct Exec {
     const Level& C = *h.lv[l + 1];
     const Grid Gf = F.grid();
     const int gb = persistent_grid(c(), Gf.ntiles);
-    if (F.stored_p) {
+    if (h.stored[l]) {
       if (F.dim == 3)
         k_prolong_w<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), pw(l), F.mask.get(),
                                                  cur[l + 1], cur[l]);
@@ -310,6 +312,12 @@ struct Exec {
   }
 };
 
+template <> const double* Exec<double, double>::c1(int l, int k) const { return &h.sc.get()->cheb_c1[l][k]; }
+template <> const double* Exec<double, double>::c2(int l, int k) const { return &h.sc.get()->cheb_c2[l][k]; }
+template <> const float* Exec<float, float>::c1(int l, int k) const { return &h.sc.get()->cheb_c1f[l][k]; }
+template <> const float* Exec<float, float>::c2(int l, int k) const { return &h.sc.get()->cheb_c2f[l][k]; }
+template <> const float* Exec<float, __nv_bfloat16>::c1(int l, int k) const { return &h.sc.get()->cheb_c1f[l][k]; }
+template <> const float* Exec<float, __nv_bfloat16>::c2(int l, int k) const { return &h.sc.get()->cheb_c2f[l][k]; }
 template <> LevelVecs<double>& Exec<double, double>::V(int l) { return h.v64[l]; }
 template <> const double* Exec<double, double>::coef(int l) const { return h.lv[l]->coef.get(); }
 template <> const double* Exec<double, double>::dinv(int l) const { return h.lv[l]->dinv.get(); }
@@ -401,6 +409,8 @@ void hier_build(Hier& h) {
     h.lv.push_back(h.own.back().get());
   }
   const int Lv = h.levels();
+  h.stored.assign(Lv, 0);
+  h.pw.resize(Lv);
   h.v64.resize(Lv);
   for (int l = 0; l < Lv; ++l) {
     h.lv[l]->dinv.ensure(h.lv[l]->n_r);   // level 0 belongs to the layout and may be shared
@@ -468,7 +478,7 @@ static void compute_dinv(Hier& h, Level& L) {
   }
 }
 
-static void galerkin(Hier& h, const Level& F, Level& C) {
+static void galerkin(Hier& h, int l, const Level& F, Level& C) {
   Ctx& c = *h.c;
   double* ap = h.layout->apbuf.get();
   const Grid Gf = F.grid(), Gc = C.grid();
@@ -489,13 +499,13 @@ static void galerkin(Hier& h, const Level& F, Level& C) {
     const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
     RMG_CUDA(cudaFuncSetAttribute(k_ap_w<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                   smem));                                                     \
-    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), F.pw.get(), \
+    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), h.pw[l].get(), \
                                                  F.mask.get(), C.mask.get(), ap);             \
   }                                                                                           \
   RMG_LAUNCHED();                                                                             \
-  k_rtap_w<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, F.pw.get(),     \
+  k_rtap_w<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, h.pw[l].get(),   \
                                               C.mask.get(), C.mult.get(), C.coef.get())
-  if (F.stored_p) {
+  if (h.stored[l]) {
     switch (F.kind) {
       case 5: RMG_RAPW(5, 9, 2); break;
       case 9: RMG_RAPW(9, 9, 2); break;
@@ -523,12 +533,13 @@ void set_transfer_weights(Hier& h, int level, const float* wr) {
               "transfer weights exist for levels 0 .. levels-2");
   Level& L = *h.lv[level];
   if (!wr) {
-    L.stored_p = false;
+    h.stored[level] = 0;
     return;
   }
-  L.pw.ensure((size_t)3 * L.n_r);
-  RMG_CUDA(cudaMemcpyAsync(L.pw.get(), wr, L.pw.bytes(), cudaMemcpyDeviceToDevice, h.c->stream));
-  L.stored_p = true;
+  h.pw[level].ensure((size_t)3 * L.n_r);
+  RMG_CUDA(cudaMemcpyAsync(h.pw[level].get(), wr, h.pw[level].bytes(), cudaMemcpyDeviceToDevice,
+                           h.c->stream));
+  h.stored[level] = 1;
 }
 
 // Operator-dependent (series-resistance) weights of a level from its current operator.
@@ -659,7 +670,7 @@ void hier_numeric(Hier& h) {
   h.coef0 = L0.coef.get();
   compute_dinv(h, *h.lv[0]);
   for (int l = 0; l + 1 < Lv; ++l) {
-    galerkin(h, *h.lv[l], *h.lv[l + 1]);
+    galerkin(h, l, *h.lv[l], *h.lv[l + 1]);
     compute_dinv(h, *h.lv[l + 1]);
   }
   if (h.o.smoother == RMG_SMOOTHER_CHEBYSHEV)
@@ -668,8 +679,7 @@ void hier_numeric(Hier& h) {
   if (h.mixed()) make_low_precision(h);
   RMG_CUDA(cudaMemcpyAsync(&h.hsc, h.sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
-  std::vector<char> stored(Lv);
-  for (int l = 0; l < Lv; ++l) stored[l] = h.lv[l]->stored_p ? 1 : 0;
+  const std::vector<char>& stored = h.stored;
   if (h.gexec && stored != h.graph_stored) {
     cudaGraphExecDestroy(h.gexec);
     cudaGraphDestroy(h.graph);

@@ -36,6 +36,11 @@ struct Hier {
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t graph_stream = nullptr;
   int launches = 0;
+  // stored transfer weights per level (to the next coarser level; linear 3:1 when not
+  // stored): pw[l][a * n_r + n] = weight of the right coarse neighbour along axis a (FP32;
+  // the entries of P are the FP32 products wz (wy wx) in every precision)
+  std::vector<char> stored;
+  std::vector<DBuf<float>> pw;
   std::vector<char> graph_stored;            // stored-transfer flags the graph was captured with
   int kind0 = 0;                             // level-0 stencil and buffer seen by the graph
   const double* coef0 = nullptr;
@@ -44,6 +49,8 @@ struct Hier {
   bool probe_pending = false;
   double probe_ms = 0.0;
   long long probe_count = 0;
+  // learned-prolongator inference scratch (features and network outputs)
+  DBuf<float> mlp_feats, mlp_out;
   // PCG work vectors (regional, FP64)
   DBuf<double> x, r, z, p, q, zold, tmp;
   double* pinned = nullptr;                  // host-mapped residual read-back

@@ -179,11 +179,6 @@ struct Level {
   DBuf<float> coef32;
   DBuf<__nv_bfloat16> coef16;
   DBuf<float> dinv32;
-  // stored transfer weights to the next coarser level (linear 3:1 when not stored):
-  // pw[a * n_r + n] = weight of the right coarse neighbour along axis a (FP32; the entries of
-  // P are the FP32 products wz (wy wx) in every precision)
-  bool stored_p = false;
-  DBuf<float> pw;
 
   Grid grid() const { return Grid{regions.get(), tiles.get(), (int)htiles.size(), nreg, n_r}; }
 };
@@ -193,6 +188,8 @@ struct Scalars {
   double lam[16];          // power-method estimate per level
   double cheb_c1[16][8];   // Chebyshev d <- c1 d + c2 D^-1 r, per level and step
   double cheb_c2[16][8];
+  float cheb_c1f[16][8];   // the same coefficients rounded to FP32 for the FP32 cycle
+  float cheb_c2f[16][8];
   double pw_norm, pw_inv;  // power method scratch (norm and its reciprocal)
   double pw_num, pw_den;
   double rz, pq, alpha, beta, rr, bb, rz_new;

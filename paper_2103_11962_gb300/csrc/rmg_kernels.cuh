@@ -152,12 +152,14 @@ struct EpiJacobi {                // u_out = u + omega D~^-1 (b - A u)
   }
 };
 
+// The Chebyshev coefficients are read in the cycle's own precision (a per-node conversion
+// from FP64 would occupy the slow FP64 pipe of the FP32 cycle).
 template <typename T>
 struct EpiCheb0 {                 // first Chebyshev step: d = D~^-1 r / theta, u_out = u + d
-  const T* u; const T* b; const T* dinv; const double* c2; T* d; T* uo;
+  const T* u; const T* b; const T* dinv; const T* c2; T* d; T* uo;
   __device__ void operator()(int n, T au, int) const {
     const T r = b[n] - au;
-    const T dn = (dinv[n] * r) * T(*c2);
+    const T dn = (dinv[n] * r) * (*c2);
     d[n] = dn;
     uo[n] = u[n] + dn;
   }
@@ -165,10 +167,10 @@ struct EpiCheb0 {                 // first Chebyshev step: d = D~^-1 r / theta, 
 
 template <typename T>
 struct EpiCheb {                  // d = c1 d + c2 D~^-1 r, u_out = u + d
-  const T* u; const T* b; const T* dinv; const double* c1; const double* c2; T* d; T* uo;
+  const T* u; const T* b; const T* dinv; const T* c1; const T* c2; T* d; T* uo;
   __device__ void operator()(int n, T au, int) const {
     const T r = b[n] - au;
-    const T dn = T(*c1) * d[n] + (T(*c2) * dinv[n]) * r;
+    const T dn = (*c1) * d[n] + ((*c2) * dinv[n]) * r;
     d[n] = dn;
     uo[n] = u[n] + dn;
   }
@@ -184,9 +186,9 @@ __global__ void k_jacobi_zero(int n, const T* __restrict__ b, const T* __restric
 
 template <typename T>
 __global__ void k_cheb0_zero(int n, const T* __restrict__ b, const T* __restrict__ dinv,
-                             const double* __restrict__ c2, T* __restrict__ d,
+                             const T* __restrict__ c2, T* __restrict__ d,
                              T* __restrict__ uo) {
-  const T c = T(*c2);
+  const T c = *c2;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const T dn = (dinv[k] * b[k]) * c;
     d[k] = dn;
@@ -211,8 +213,16 @@ __host__ __device__ constexpr double wrem(int rem, int side) {
 // Region-local restriction w = [[R]] rs for every coarse node, rs = r / mult being the
 // residual already scaled by [[Psi Psi^T]]^-1. Zero at masked coarse nodes (their column of
 // P is zero). Shared coarse nodes store into yc for the coarse interface sum.
-template <int DIM, bool CHECK, typename VT>
+template <typename T, typename W>
+__device__ __forceinline__ T pw_seen_from_coarse(const W* __restrict__ wr, int n_f, int f,
+                                                 int axis, int off);
+
+// sum over the fine nodes f = 3C + (a, b, c) of the support of coarse node C of P(f, C) rs[f];
+// P(f, C) is a compile-time constant for linear interpolation (STORED = false) or the FP32
+// product of the stored per-axis weights of f.
+template <int DIM, bool CHECK, bool STORED, typename VT>
 __device__ __forceinline__ VT restrict_sum(const VT* __restrict__ rs, const RegionDev& F,
+                                           const float* __restrict__ wr, int fn_r,
                                            int I, int J, int L) {
   VT acc = VT(0);
   constexpr int ZL = DIM == 3 ? -2 : 0, ZH = DIM == 3 ? 2 : 0;
@@ -229,9 +239,15 @@ __device__ __forceinline__ VT restrict_sum(const VT* __restrict__ rs, const Regi
       for (int a = -2; a <= 2; ++a) {
         const int fx = 3 * I + a;
         if (CHECK && (fx < 0 || fx >= F.nx)) continue;
-        constexpr double dummy = 0.0;
-        (void)dummy;
-        const VT wgt = VT((DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a)));
+        VT wgt;
+        if (STORED) {
+          const int f = row + fx;
+          const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
+          wgt = VT(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
+                         pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
+        } else {
+          wgt = VT((DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a)));
+        }
         acc = fma(wgt, rs[row + fx], acc);
       }
     }
@@ -252,8 +268,8 @@ k_restrict(Grid Gc, const RegionDev* __restrict__ fregions, const VT* __restrict
       const RegionDev F = fregions[tile_.region];
       const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
                          (DIM == 2 || (L > 0 && L < R.nz - 1));
-      acc = inner ? restrict_sum<DIM, false, VT>(rs, F, I, J, L)
-                  : restrict_sum<DIM, true, VT>(rs, F, I, J, L);
+      acc = inner ? restrict_sum<DIM, false, false, VT>(rs, F, nullptr, 0, I, J, L)
+                  : restrict_sum<DIM, true, false, VT>(rs, F, nullptr, 0, I, J, L);
     }
     if (cmult[n] > 1) yc[n] = acc; else w[n] = acc;
   RMG_END_FOR_NODES
@@ -317,24 +333,10 @@ k_restrict_w(Grid Gc, const RegionDev* __restrict__ fregions, int fn_r, const fl
     VT acc = VT(0);
     if (!cmask[n]) {
       const RegionDev F = fregions[tile_.region];
-      const int zl = DIM == 3 ? -2 : 0, zh = DIM == 3 ? 2 : 0;
-      for (int c = zl; c <= zh; ++c) {
-        const int fz = DIM == 3 ? 3 * L + c : 0;
-        if (fz < 0 || fz >= F.nz) continue;
-        for (int b = -2; b <= 2; ++b) {
-          const int fy = 3 * J + b;
-          if (fy < 0 || fy >= F.ny) continue;
-          for (int a = -2; a <= 2; ++a) {
-            const int fx = 3 * I + a;
-            if (fx < 0 || fx >= F.nx) continue;
-            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-            const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
-            const float wgt = wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
-                                    pw_seen_from_coarse<float>(wr, fn_r, f, 0, a));
-            acc = fma(VT(wgt), rs[f], acc);
-          }
-        }
-      }
+      const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
+                         (DIM == 2 || (L > 0 && L < R.nz - 1));
+      acc = inner ? restrict_sum<DIM, false, true, VT>(rs, F, wr, fn_r, I, J, L)
+                  : restrict_sum<DIM, true, true, VT>(rs, F, wr, fn_r, I, J, L);
     }
     if (cmult[n] > 1) yc[n] = acc; else w[n] = acc;
   RMG_END_FOR_NODES

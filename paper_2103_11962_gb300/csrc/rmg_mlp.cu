@@ -16,6 +16,8 @@
 // copies of a node, so co-located copies see the same features and get identical weights.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "rmg_hier.cuh"
 #include "rmg_kernels.cuh"
 
@@ -87,7 +89,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 // mode 0: inference (rows = samples base..base+127, outputs written to out[n][3]).
 // mode 1: gradient (rows sampled or taken in order; gradients and loss accumulated).
 __global__ void __launch_bounds__(kThreads)
-k_mlp(const float* __restrict__ params, int n, const float* __restrict__ feats,
+k_mlp(const float* __restrict__ params, int n, long long ntiles, const float* __restrict__ feats,
       const float* __restrict__ labels, const float* __restrict__ mask, int mode, int sample,
       unsigned long long seed, float inv_norm, float* __restrict__ out, float* __restrict__ grads,
       float* __restrict__ loss) {
@@ -95,7 +97,6 @@ k_mlp(const float* __restrict__ params, int n, const float* __restrict__ feats,
   MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const long long base = (long long)blockIdx.x * kRows;
 
   // ---- stage weights (bf16 copies for the MMA, fp32 copies for the backward pass)
   for (int e = tid; e < NH * NF; e += kThreads)
@@ -111,6 +112,10 @@ k_mlp(const float* __restrict__ params, int n, const float* __restrict__ feats,
     S.W3b[j * SH + k] = __float2bfloat16_rn(w);
     if (j < NOUT) S.W3f[j * NH + k] = w;
   }
+  // persistent loop over tiles of 128 samples; the weights above are staged once per CTA
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const long long base = tile * kRows;
+  __syncthreads();
   // ---- stage the samples
   for (int e = tid; e < kRows * NF; e += kThreads) {
     const int r = e / NF, k = e % NF;
@@ -191,7 +196,7 @@ k_mlp(const float* __restrict__ params, int n, const float* __restrict__ feats,
       const int r = e / NOUT, j = e % NOUT;
       if (base + r < n) out[(base + r) * NOUT + j] = S.O[r * 4 + j];
     }
-    return;
+    continue;
   }
 
   // ---- backward (FP32 CUDA cores)
@@ -264,6 +269,7 @@ k_mlp(const float* __restrict__ params, int n, const float* __restrict__ feats,
     for (int r = 0; r < kRows; ++r) s += S.dZ1[r * SD + tid];
     atomicAdd(&grads[O_B1 + tid], s);
   }
+  }  // tiles
 }
 
 __global__ void k_adam(int np, float* __restrict__ p, const float* __restrict__ gr,
@@ -303,17 +309,18 @@ k_features(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ 
         continue;
       }
       const int p0 = n - rem * stride[a];
+      // ratios in FP64, logarithms in FP32 (the features are FP32 network inputs)
       for (int e = 0; e < 3; ++e) {
         const double k = -comp_coupling<KIND>(coef, G.n_r, p0 + e * stride[a], slot, mult, gid,
                                               cgrp, gptr, gslot);
-        const double v = log10(fmax(k / dref, 1e-12));
-        f[9 * a + e] = (float)fmin(v, 2.0);
+        const float v = log10f(fmaxf((float)(k / dref), 1e-12f));
+        f[9 * a + e] = fminf(v, 2.f);
       }
       for (int i = 0; i < 4; ++i) {
         const double d = comp_coupling<KIND>(coef, G.n_r, p0 + i * stride[a], St::CENTER, mult,
                                              gid, cgrp, gptr, gslot);
-        const double v = log10(fmax(d / dref, 1e-12));
-        f[9 * a + 3 + i] = (float)fmin(v, 12.0);
+        const float v = log10f(fmaxf((float)(d / dref), 1e-12f));
+        f[9 * a + 3 + i] = fminf(v, 12.f);
       }
       f[9 * a + 7] = (float)(rem / 3.0);
       f[9 * a + 8] = 1.f;
@@ -367,9 +374,10 @@ void mlp_launch(rmg_mlp* net, int n, const float* feats, const float* labels, co
   Ctx& c = net->ctx->c;
   const int smem = (int)mlp_smem();
   RMG_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const int blocks = (rows + kRows - 1) / kRows;
-  k_mlp<<<blocks, kThreads, smem, c.stream>>>(net->p.get(), n, feats, labels, mask, mode, sample,
-                                             seed, inv_norm, out, net->g.get(), loss);
+  const long long tiles = (rows + kRows - 1) / kRows;
+  const int blocks = (int)std::min<long long>(tiles, (long long)c.nsm * 2);
+  k_mlp<<<blocks, kThreads, smem, c.stream>>>(net->p.get(), n, tiles, feats, labels, mask, mode,
+                                             sample, seed, inv_norm, out, net->g.get(), loss);
   RMG_LAUNCHED();
 }
 }  // namespace
@@ -488,24 +496,22 @@ rmg_status rmg_hier_mlp_features(rmg_hier* hh, int level, float* feats) {
 
 rmg_status rmg_hier_mlp_weights(rmg_hier* hh, int level, rmg_mlp* net, float* wr) {
   if (!hh || !net) return RMG_ERR_ARG;
-  rmg_status st = RMG_OK;
   Hier& h = hh->h;
   const int n_r = (level >= 0 && level < h.levels()) ? h.lv[level]->n_r : 0;
-  DBuf<float> feats, out;
-  st = mlp_guard(h.layout->ctx, [&] {
+  rmg_status st = mlp_guard(h.layout->ctx, [&] {
     RMG_REQUIRE(n_r > 0 && wr, RMG_ERR_ARG, "bad arguments");
-    feats.alloc((size_t)n_r * NF);
-    out.alloc((size_t)n_r * 3);
+    h.mlp_feats.ensure((size_t)h.lv[0]->n_r * NF);       // sized for the finest level, kept
+    h.mlp_out.ensure((size_t)h.lv[0]->n_r * 3);
   });
   if (st != RMG_OK) return st;
-  st = rmg_hier_mlp_features(hh, level, feats.get());
+  st = rmg_hier_mlp_features(hh, level, h.mlp_feats.get());
   if (st != RMG_OK) return st;
   return mlp_guard(h.layout->ctx, [&] {
-    mlp_launch(net, n_r, feats.get(), nullptr, nullptr, 0, 0, n_r, 0, 0.f, out.get(), nullptr);
+    mlp_launch(net, n_r, h.mlp_feats.get(), nullptr, nullptr, 0, 0, n_r, 0, 0.f,
+               h.mlp_out.get(), nullptr);
     k_weights_from_out<<<persistent_grid(*h.c, (n_r + 255) / 256), 256, 0, h.c->stream>>>(
-        n_r, feats.get(), out.get(), wr);
+        n_r, h.mlp_feats.get(), h.mlp_out.get(), wr);
     RMG_LAUNCHED();
-    RMG_CUDA(cudaStreamSynchronize(h.c->stream));
   });
 }
 

@@ -123,10 +123,10 @@ k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fc
   RMG_END_FOR_NODES
 }
 
-template <int DIM, bool CHECK>
+template <int DIM, bool CHECK, bool STORED>
 __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r,
-                                         const RegionDev& F, int I, int J, int L,
-                                         double (&acc)[27]) {
+                                         const RegionDev& F, const float* __restrict__ wr,
+                                         int I, int J, int L, double (&acc)[27]) {
   constexpr int ZL = DIM == 3 ? -2 : 0, ZH = DIM == 3 ? 2 : 0;
 #pragma unroll
   for (int c = ZL; c <= ZH; ++c) {
@@ -141,7 +141,14 @@ __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r
         const int fx = 3 * I + a;
         if (CHECK && (fx < 0 || fx >= F.nx)) continue;
         const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-        const double wf = (DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a));
+        double wf;
+        if (STORED) {
+          const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
+          wf = (double)(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
+                              pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
+        } else {
+          wf = (DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a));
+        }
         // ap of node f is stored relative to the coarse node (f - 1) div 3 on each axis,
         // which is C - 1 for offsets a <= 0 and C for a >= 1
         const int bx = a <= 0 ? 1 : 0, by = b <= 0 ? 1 : 0, bz = DIM == 3 ? (c <= 0 ? 1 : 0) : 0;
@@ -179,8 +186,8 @@ k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ 
       const RegionDev F = fregs[tile_.region];
       const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
                          (DIM == 2 || (L > 0 && L < R.nz - 1));
-      if (inner) rtap_sum<DIM, false>(ap, fn_r, F, I, J, L, acc);
-      else rtap_sum<DIM, true>(ap, fn_r, F, I, J, L, acc);
+      if (inner) rtap_sum<DIM, false, false>(ap, fn_r, F, nullptr, I, J, L, acc);
+      else rtap_sum<DIM, true, false>(ap, fn_r, F, nullptr, I, J, L, acc);
     }
 #pragma unroll
     for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
@@ -252,35 +259,10 @@ k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict_
       int I, J, L;
       decode(li, R, I, J, L);
       const RegionDev F = fregs[tile_.region];
-      for (int c = (DIM == 3 ? -2 : 0); c <= (DIM == 3 ? 2 : 0); ++c) {
-        const int fz = DIM == 3 ? 3 * L + c : 0;
-        if (fz < 0 || fz >= F.nz) continue;
-        for (int b = -2; b <= 2; ++b) {
-          const int fy = 3 * J + b;
-          if (fy < 0 || fy >= F.ny) continue;
-          for (int a = -2; a <= 2; ++a) {
-            const int fx = 3 * I + a;
-            if (fx < 0 || fx >= F.nx) continue;
-            const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-            const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
-            const double wf = (double)(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
-                                             pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
-            if (wf == 0.0) continue;
-            const int bx = a <= 0 ? 1 : 0, by = b <= 0 ? 1 : 0, bz = DIM == 3 ? (c <= 0 ? 1 : 0) : 0;
-#pragma unroll
-            for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
-#pragma unroll
-              for (int oy = -1; oy <= 1; ++oy)
-#pragma unroll
-                for (int ox = -1; ox <= 1; ++ox) {
-                  const int ix = ox + bx, iy = oy + by, iz = oz + bz;
-                  if (ix < 0 || ix > 2 || iy < 0 || iy > 2 || iz < 0 || iz > 2) continue;
-                  const int slot = (ox + 1) + 3 * (oy + 1) + (DIM == 3 ? 9 * (oz + 1) : 0);
-                  acc[slot] = fma(wf, ap[(size_t)(ix + 3 * iy + 9 * iz) * fn_r + f], acc[slot]);
-                }
-          }
-        }
-      }
+      const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
+                         (DIM == 2 || (L > 0 && L < R.nz - 1));
+      if (inner) rtap_sum<DIM, false, true>(ap, fn_r, F, wr, I, J, L, acc);
+      else rtap_sum<DIM, true, true>(ap, fn_r, F, wr, I, J, L, acc);
     }
 #pragma unroll
     for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
@@ -391,6 +373,10 @@ __global__ void k_cheb_coeffs(Scalars* sc, int level, double eig_ratio, double b
     rho = 1.0 / (2.0 * theta * delta - rho_old);
     sc->cheb_c1[level][k] = rho * rho_old;
     sc->cheb_c2[level][k] = 2.0 * rho * delta;
+  }
+  for (int k = 0; k < 8; ++k) {
+    sc->cheb_c1f[level][k] = (float)sc->cheb_c1[level][k];
+    sc->cheb_c2f[level][k] = (float)sc->cheb_c2[level][k];
   }
 }
 
