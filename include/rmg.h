@@ -137,6 +137,19 @@ rmg_status rmg_layout_sizes(rmg_layout* layout, int64_t* n_regional, int64_t* n_
 rmg_status rmg_operator_from_csr(rmg_layout* layout, int stencil, const int64_t* rowptr,
                                  const int64_t* col, const double* val);
 
+/* Block operators with dofs_per_node = 3 (3D linear elasticity: 3x3 blocks per stencil
+ * offset, 81 coefficients per dof row with a 27-point stencil). The composite CSR numbers
+ * dofs node-major (row/column g * 3 + c). Every 3x3 block (c, c') is split by the rule of
+ * rmg_operator_from_csr applied to the scalar matrix A[c::3, c'::3]; for the translations
+ * (the rigid-body nullspace used by the paper's draft appendix rule) this keeps
+ * sum_k A^(k) = A block by block. Transfers are the scalar 3:1 interpolation on every
+ * component, so the coarse operators are again 3x3-block 27-point (9-point in 2D) stencils.
+ * Regional vectors of such a layout are component-major: entry c * n_r + n; composite
+ * vectors are node-major (g * 3 + c). The stencil must be 27 (3D) or 9 (2D). */
+rmg_status rmg_operator_from_block_csr(rmg_layout* layout, int stencil, int dofs_per_node,
+                                       const int64_t* rowptr, const int64_t* col,
+                                       const double* val);
+
 /* Set already-split region matrices directly: coeffs is device double[stencil * n_r],
  * slot-major (coefficient s of regional node n at s * n_r + n). Slot order: 7-point
  * (-z,-y,-x,0,+x,+y,+z); 5-point (-y,-x,0,+x,+y); 9/27-point: (dx+1) + 3(dy+1) [+ 9(dz+1)]. */
@@ -285,16 +298,20 @@ rmg_status rmg_regional_apply_static(int dim, int nregions, const int32_t* regio
 /* Levels, and per level: regions, regional nodes, composite id space, stencil points. */
 rmg_status rmg_hier_level_sizes(rmg_hier* hier, int level, int64_t* n_regional,
                                 int64_t* n_composite, int* stencil);
+/* Dofs per node of the hierarchy's operator (1, or 3 for block operators). */
+rmg_status rmg_hier_dofs_per_node(rmg_hier* hier, int* dofs);
 /* Copy level data to caller device buffers (any may be NULL):
- *   coeffs  double[stencil * n_r] region stencils (slot-major, see above), FP64 copy
- *   dinv    double[n_r] inverse composite diagonal in regional layout
+ *   coeffs  double[B * B * stencil * n_r] region stencils (slot-major, see above; block
+ *           (c, c') of a B-dof operator at offset (c * B + c') * stencil * n_r), FP64 copy
+ *   dinv    double[B * n_r] inverse composite diagonal in regional layout (component-major)
  *   gids    int64[n_r] composite id of every regional node on that level */
 rmg_status rmg_hier_level_export(rmg_hier* hier, int level, double* coeffs, double* dinv,
                                  int64_t* gids);
 /* Chebyshev lambda~ estimate of a level (host). */
 rmg_status rmg_hier_lambda(rmg_hier* hier, int level, double* lam);
 /* Coarsest composite matrix restricted to unmasked nodes (dense, row-major, host double
- * [nc*nc]) and the composite ids of those unknowns (host int64[nc]). Pass NULL to query nc. */
+ * [(B*nc)^2], dof cu * B + c) and the composite ids of those nodes (host int64[nc]). Pass NULL
+ * to query nc (the number of unmasked composite nodes). */
 rmg_status rmg_hier_coarse_matrix(rmg_hier* hier, int64_t* nc, double* dense, int64_t* ids);
 /* Kernels launched by this library in this process so far (a graph replay counts the
  * kernels of the graph). Kernels recorded into a graph during capture are not counted. */

@@ -58,7 +58,7 @@ class CoarseSolver:
 
 def power_start(level: Level, l: int, opts: Options):
     """Composite start vector: SplitMix64 stream (seed_base + l) indexed by composite id."""
-    x = uniform_pm1(opts.power_seed_base + l, np.arange(level.layout.n))
+    x = uniform_pm1(opts.power_seed_base + l, level.layout.counter_ids())
     x[level.layout.mask] = 0.0
     return x
 

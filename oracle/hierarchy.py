@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-from .regions import Layout, make_layout, block_diag
+from .regions import Layout, make_layout, block_diag, block_layout
 from .split import split_regional
 from .transfer import composite_p, coarse_count, coarse_mask_from_fine, regional_p, stored_p
 
@@ -105,6 +105,54 @@ def build(problem_or_parts, nlevels: int, regional: bool = True, weights=None):
         if regional:
             dr = lev.layout.interface_sum(lev.Ar.diagonal())
             lev.Dinv_r = 1.0 / dr
+    return levels
+
+
+def node_major_to_component_major(n_nodes: int, B: int) -> np.ndarray:
+    """Permutation: component-major entry c * n + g takes node-major dof g * B + c."""
+    g = np.tile(np.arange(n_nodes), B)
+    c = np.repeat(np.arange(B), n_nodes)
+    return g * B + c
+
+
+def build_block(p, nlevels: int):
+    """Hierarchies of a B-dof operator (elasticity) in component-major ordering.
+
+    The split acts on every B x B block A_cc' = A[c::B, c'::B] with the scalar rule (for the
+    translations of the draft appendix's nullspace rule this is the scalar rule per block);
+    the transfers are I_B (x) P with the scalar 3:1 interpolation; Galerkin products as usual.
+    """
+    B = p.dofs_per_node
+    dims = tuple(int(v) for v in p.global_dims)
+    n = int(np.prod(dims))
+    slay = make_layout(p.region_dims, p.region_gids, n, p.dirichlet)
+    perm = node_major_to_component_major(n, B)
+    A = sp.csr_matrix(p.A)[perm][:, perm].tocsr()
+    blocks = [[split_regional(slay, A[c * n:(c + 1) * n, c2 * n:(c2 + 1) * n])
+               for c2 in range(B)] for c in range(B)]
+    lay = block_layout(slay, B)
+    lev0 = Level(dims=dims, layout=lay, A=A, Ar=sp.bmat(blocks, format="csr"))
+    lev0.extra["slay"] = slay
+    levels = [lev0]
+    I = sp.identity(B, format="csr")
+    for l in range(nlevels - 1):
+        f = levels[l]
+        fs = f.extra["slay"]
+        cdims, cs = inject_layout(fs, f.dims)
+        Pn = composite_p(f.dims, fs.mask, cs.mask)
+        f.P = sp.kron(I, Pn).tocsr()
+        f.Pr = sp.kron(I, regional_p(fs, cs, Pn)).tocsr()
+        clay = block_layout(cs, B)
+        Ac = _identity_on_mask((f.P.T @ f.A @ f.P).tocsr(), clay.mask.astype(float))
+        Arc = (f.Pr.T @ f.Ar @ f.Pr).tocsr()
+        rmask = clay.regional_mask()
+        c = Level(dims=cdims, layout=clay, A=Ac,
+                  Ar=_identity_on_mask(Arc, np.where(rmask, 1.0 / clay.regional_mult(), 0.0)))
+        c.extra["slay"] = cs
+        levels.append(c)
+    for lev in levels:
+        lev.Dinv = 1.0 / lev.A.diagonal()
+        lev.Dinv_r = 1.0 / lev.layout.interface_sum(lev.Ar.diagonal())
     return levels
 
 

@@ -65,6 +65,10 @@ class Layout:
         """Composite inner product of two consistent regional vectors: sum x y / mult."""
         return float(np.sum(xr * yr / self.regional_mult()))
 
+    def counter_ids(self):
+        """Composite dof id of every composite vector entry (the power-method counters)."""
+        return np.arange(self.n)
+
 
 def make_layout(region_dims, region_gids, n, mask) -> Layout:
     region_dims = np.asarray(region_dims, dtype=np.int64)
@@ -92,3 +96,30 @@ def incidence(layout: Layout) -> sp.csr_matrix:
 
 def block_diag(blocks):
     return sp.block_diag(blocks, format="csr")
+
+
+@dataclass
+class BlockLayout(Layout):
+    """B dofs per node, vectors component-major (entry c * n + g): Psi_B = I_B (x) Psi."""
+    B: int = 1
+    scalar: Layout = None
+
+    @property
+    def n_r(self):
+        return int(self.region_gids.shape[0]) * self.B
+
+    def regional_mask(self):
+        return np.tile(self.scalar.regional_mask(), self.B)
+
+    def counter_ids(self):
+        """Entry c * n + g is composite dof g * B + c (dofs numbered node-major)."""
+        ns = self.scalar.n
+        g = np.tile(np.arange(ns), self.B)
+        c = np.repeat(np.arange(self.B), ns)
+        return g * self.B + c
+
+
+def block_layout(lay: Layout, B: int) -> BlockLayout:
+    Psi = sp.kron(sp.identity(B, format="csr"), lay.Psi).tocsr()
+    return BlockLayout(lay.region_dims, lay.region_gids, lay.n * B, lay.offsets, Psi, None,
+                       np.tile(lay.mult, B), np.tile(lay.mask, B), B=B, scalar=lay)

@@ -123,7 +123,18 @@ rmg_status rmg_operator_from_csr(rmg_layout* lay, int stencil, const int64_t* ro
                                  const int64_t* col, const double* val) {
   if (!lay) return RMG_ERR_ARG;
   return guarded(lay->ctx, [&] {
-    split_from_csr(lay->ctx->c, lay->L0, stencil, rowptr, col, val);
+    split_from_csr(lay->ctx->c, lay->L0, stencil, 1, rowptr, col, val);
+    lay->has_operator = true;
+  });
+}
+
+rmg_status rmg_operator_from_block_csr(rmg_layout* lay, int stencil, int dofs_per_node,
+                                       const int64_t* rowptr, const int64_t* col,
+                                       const double* val) {
+  if (!lay) return RMG_ERR_ARG;
+  return guarded(lay->ctx, [&] {
+    split_from_csr(lay->ctx->c, lay->L0, stencil, dofs_per_node, rowptr, col, val);
+    lay->ybuf.ensure((size_t)dofs_per_node * lay->L0.n_r);
     lay->has_operator = true;
   });
 }
@@ -226,6 +237,12 @@ rmg_status rmg_hier_level_sizes(rmg_hier* hh, int level, int64_t* n_regional, in
   return RMG_OK;
 }
 
+rmg_status rmg_hier_dofs_per_node(rmg_hier* hh, int* dofs) {
+  if (!hh || !dofs) return RMG_ERR_ARG;
+  *dofs = hh->h.lv[0]->B;
+  return RMG_OK;
+}
+
 namespace {
 __global__ void k_int_to_i64(int n, const int* a, int64_t* b) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = a[k];
@@ -240,6 +257,7 @@ rmg_status rmg_hier_level_export(rmg_hier* hh, int level, double* coeffs, double
     RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
     Level& L = *h.lv[level];
     cudaStream_t st = h.c->stream;
+    // coefficients: B*B*stencil*n_r (block (c,c') at offset (c*B+c')*stencil*n_r); dinv: B*n_r
     if (coeffs)
       RMG_CUDA(cudaMemcpyAsync(coeffs, L.coef.get(), L.coef.bytes(), cudaMemcpyDeviceToDevice, st));
     if (dinv)
@@ -286,9 +304,9 @@ rmg_status rmg_hier_coarse_matrix(rmg_hier* hh, int64_t* nc, double* dense, int6
   return guarded(hh->h.layout->ctx, [&] {
     Hier& h = hh->h;
     *nc = h.nc;
+    const size_t nd = (size_t)h.nc * h.lv[h.levels() - 1]->B;
     if (dense && h.nc)
-      RMG_CUDA(cudaMemcpy(dense, h.X.get(), (size_t)h.nc * h.nc * sizeof(double),
-                          cudaMemcpyDeviceToHost));
+      RMG_CUDA(cudaMemcpy(dense, h.X.get(), nd * nd * sizeof(double), cudaMemcpyDeviceToHost));
     if (ids && h.nc)
       RMG_CUDA(cudaMemcpy(ids, h.cu2gid.get(), (size_t)h.nc * sizeof(long long),
                           cudaMemcpyDeviceToHost));

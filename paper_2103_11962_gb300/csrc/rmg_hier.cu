@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "rmg_hier.cuh"
+#include "rmg_launch.cuh"
 #include "rmg_layout.cuh"
 #include "rmg_setup_kernels.cuh"
 
@@ -38,10 +39,10 @@ __global__ void k_to_bf16(size_t n, const double* __restrict__ a, __nv_bfloat16*
 
 // coarse solve: gather the averaged composite right-hand side, x = Abar^-1 rhs, replicate
 template <typename VT>
-__global__ void k_coarse_gather(int nc, const VT* __restrict__ w, const int* __restrict__ cu2slot,
-                                double* __restrict__ rc) {
+__global__ void k_coarse_gather(int nc, int B, int n_r, const VT* __restrict__ w,
+                                const int* __restrict__ cu2slot, double* __restrict__ rc) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x)
-    rc[k] = double(w[cu2slot[k]]);
+    for (int b = 0; b < B; ++b) rc[(size_t)k * B + b] = double(w[(size_t)b * n_r + cu2slot[k]]);
 }
 
 __global__ void k_gemv(int nc, const double* __restrict__ A, const double* __restrict__ v,
@@ -60,11 +61,13 @@ __global__ void k_gemv(int nc, const double* __restrict__ A, const double* __res
 }
 
 template <typename VT>
-__global__ void k_coarse_scatter(int n_r, const int* __restrict__ gid, const int* __restrict__ cidx,
-                                 const double* __restrict__ xc, VT* __restrict__ u) {
+__global__ void k_coarse_scatter(int n_r, int B, const int* __restrict__ gid,
+                                 const int* __restrict__ cidx, const double* __restrict__ xc,
+                                 VT* __restrict__ u) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x) {
     const int c = cidx[gid[k]];
-    u[k] = c >= 0 ? VT(xc[c]) : VT(0);
+    for (int b = 0; b < B; ++b)
+      u[(size_t)b * n_r + k] = c >= 0 ? VT(xc[(size_t)c * B + b]) : VT(0);
   }
 }
 
@@ -78,7 +81,7 @@ __global__ void k_beta(Scalars* sc, int flexible) {
 }
 
 __global__ void __launch_bounds__(256)
-k_cg_update(int n, const double* __restrict__ p, const double* __restrict__ q,
+k_cg_update(int n, int n_nodes, const double* __restrict__ p, const double* __restrict__ q,
             const uint8_t* __restrict__ mult, const Scalars* __restrict__ sc,
             double* __restrict__ x, double* __restrict__ r, double* __restrict__ partials) {
   const double a = sc->alpha;
@@ -87,7 +90,7 @@ k_cg_update(int n, const double* __restrict__ p, const double* __restrict__ q,
     x[k] = x[k] + a * p[k];
     const double rk = r[k] - a * q[k];
     r[k] = rk;
-    s += (rk * rk) * inv_mult<double>(mult[k]);
+    s += (rk * rk) * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]);
   }
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -105,35 +108,12 @@ __global__ void k_p_update(int n, const double* __restrict__ z, const Scalars* _
     p[k] = z[k] + b * p[k];
 }
 
-template <class Epi, typename CT, typename VT, typename AT>
-void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
-                    cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
-                    cudaEvent_t ev1 = nullptr) {
-  const Grid G = L.grid();
-  const int gb = persistent_grid(c, G.ntiles);
-  // external record nodes when capturing, so the events can be timed after a graph replay
-  if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));
-  switch (L.kind) {
-    case 5: k_stencil<5, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
-    case 7: k_stencil<7, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
-    case 9: k_stencil<9, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
-    default: k_stencil<27, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
-  }
-  RMG_LAUNCHED();
-  if (ev1) RMG_CUDA(cudaEventRecordWithFlags(ev1, st, g_capturing ? cudaEventRecordExternal : 0));
-  if (launches) ++*launches;
-  if (L.ngroups) {
-    k_groups<AT><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, st>>>(
-        L.ngroups, L.gptr.get(), L.gslot.get(), y, epi);
-    RMG_LAUNCHED();
-    if (launches) ++*launches;
-  }
-}
-
-void dot(Ctx& c, int n, const double* x, const double* y, const uint8_t* mult, double* dst,
-         int op, cudaStream_t st) {
+// Composite inner product of consistent regional vectors with n entries (B components of
+// n_nodes nodes each, component-major).
+void dot(Ctx& c, int n, int n_nodes, const double* x, const double* y, const uint8_t* mult,
+         double* dst, int op, cudaStream_t st) {
   const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
-  k_dot<double, double><<<g, 256, 0, st>>>(n, x, y, mult, c.partials.get());
+  k_dot<double, double><<<g, 256, 0, st>>>(n, n_nodes, x, y, mult, c.partials.get());
   RMG_LAUNCHED();
   k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, dst, op);
   RMG_LAUNCHED();
@@ -180,7 +160,7 @@ struct Exec {
 
   void smooth(int l, int nu, bool from_zero, bool probe_it = false) {
     const Level& L = *h.lv[l];
-    const int n = L.n_r;
+    const int n = L.B * L.n_r;
     const VT omega = VT(h.o.omega);
     if (h.o.smoother == RMG_SMOOTHER_JACOBI) {
       for (int s = 0; s < nu; ++s) {
@@ -222,6 +202,26 @@ struct Exec {
   void restrict_to(int l) {
     const Level& F = *h.lv[l];
     const Level& C = *h.lv[l + 1];
+    if (F.B > 1) {   // B x B block operators: the scalar transfer on every component
+      const Grid Gc = C.grid();
+      const int gb = persistent_grid(c(), Gc.ntiles);
+      for (int b = 0; b < F.B; ++b) {
+        VT* wb = V(l + 1).b.get() + (size_t)b * C.n_r;
+        VT* yb = V(l + 1).y.get() + (size_t)b * C.n_r;
+        const VT* rb = V(l).r.get() + (size_t)b * F.n_r;
+        k_restrict<3, VT><<<gb, kTile, 0, st>>>(Gc, F.regions.get(), rb, C.mask.get(),
+                                                C.mult.get(), wb, yb);
+        RMG_LAUNCHED();
+        ++launches;
+        if (C.ngroups) {
+          k_groups<VT><<<persistent_grid(c(), (C.ngroups + 255) / 256), 256, 0, st>>>(
+              C.ngroups, C.gptr.get(), C.gslot.get(), yb, EpiStore<VT>{wb});
+          RMG_LAUNCHED();
+          ++launches;
+        }
+      }
+      return;
+    }
     const Grid Gc = C.grid();
     const int gb = persistent_grid(c(), Gc.ntiles);
     if (h.stored[l]) {
@@ -254,6 +254,16 @@ struct Exec {
     const Level& C = *h.lv[l + 1];
     const Grid Gf = F.grid();
     const int gb = persistent_grid(c(), Gf.ntiles);
+    if (F.B > 1) {
+      for (int b = 0; b < F.B; ++b) {
+        k_prolong<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), F.mask.get(),
+                                               cur[l + 1] + (size_t)b * C.n_r,
+                                               cur[l] + (size_t)b * F.n_r);
+        RMG_LAUNCHED();
+        ++launches;
+      }
+      return;
+    }
     if (h.stored[l]) {
       if (F.dim == 3)
         k_prolong_w<3, VT><<<gb, kTile, 0, st>>>(Gf, C.regions.get(), pw(l), F.mask.get(),
@@ -273,17 +283,17 @@ struct Exec {
     const Level& L = *h.lv[l];
     const int nc = h.nc;
     if (nc > 0) {
-      k_coarse_gather<VT><<<elementwise_grid(nc), 256, 0, st>>>(nc, V(l).b.get(), h.cu2slot.get(),
-                                                                h.rc.get());
+      k_coarse_gather<VT><<<elementwise_grid(nc), 256, 0, st>>>(nc, L.B, L.n_r, V(l).b.get(),
+                                                                h.cu2slot.get(), h.rc.get());
       RMG_LAUNCHED();
-      const int warps_needed = nc;
-      const int blocks = std::max(1, std::min(c().nsm * 4, (warps_needed * 32 + 255) / 256));
-      k_gemv<<<blocks, 256, 0, st>>>(nc, h.Ainv.get(), h.rc.get(), h.xc.get());
+      const int nd = nc * L.B;
+      const int blocks = std::max(1, std::min(c().nsm * 4, (nd * 32 + 255) / 256));
+      k_gemv<<<blocks, 256, 0, st>>>(nd, h.Ainv.get(), h.rc.get(), h.xc.get());
       RMG_LAUNCHED();
       launches += 2;
     }
-    k_coarse_scatter<VT><<<elementwise_grid(L.n_r), 256, 0, st>>>(L.n_r, L.gid.get(), h.cidx.get(),
-                                                                  h.xc.get(), cur[l]);
+    k_coarse_scatter<VT><<<elementwise_grid(L.n_r), 256, 0, st>>>(L.n_r, L.B, L.gid.get(),
+                                                                  h.cidx.get(), h.xc.get(), cur[l]);
     RMG_LAUNCHED();
     ++launches;
   }
@@ -387,7 +397,8 @@ static void coarsen_level(Hier& h, const Level& F, Level& C) {
   build_groups(c, C, nullptr, cmask.get(), count);
   c.check_device_error("rmg_setup");
   C.kind = coarse_kind(F.kind);
-  C.coef.alloc((size_t)C.kind * C.n_r);
+  C.B = F.B;
+  C.coef.alloc((size_t)C.B * C.B * C.kind * C.n_r);
 }
 
 void hier_build(Hier& h) {
@@ -413,23 +424,24 @@ void hier_build(Hier& h) {
   h.pw.resize(Lv);
   h.v64.resize(Lv);
   for (int l = 0; l < Lv; ++l) {
-    h.lv[l]->dinv.ensure(h.lv[l]->n_r);   // level 0 belongs to the layout and may be shared
-    h.v64[l].alloc(h.lv[l]->n_r);
+    const size_t nb = (size_t)h.lv[l]->B * h.lv[l]->n_r;
+    h.lv[l]->dinv.ensure(nb);   // level 0 belongs to the layout and may be shared
+    h.v64[l].alloc((int)nb);
   }
   if (h.mixed()) {
     h.v32.resize(Lv);
     for (int l = 0; l < Lv; ++l) {
       Level& L = *h.lv[l];
-      h.v32[l].alloc(L.n_r);
-      L.dinv32.ensure(L.n_r);
-      if (o.precision == RMG_PREC_FP32) L.coef32.ensure((size_t)L.kind * L.n_r);
-      else L.coef16.ensure((size_t)L.kind * L.n_r);
+      h.v32[l].alloc(L.B * L.n_r);
+      L.dinv32.ensure((size_t)L.B * L.n_r);
+      if (o.precision == RMG_PREC_FP32) L.coef32.ensure((size_t)L.B * L.B * L.kind * L.n_r);
+      else L.coef16.ensure((size_t)L.B * L.B * L.kind * L.n_r);
     }
   }
   if (Lv > 1) h.layout->apbuf.ensure((size_t)(h.lv[0]->dim == 3 ? 27 : 9) * h.lv[0]->n_r);
   h.sc.alloc(1);
   RMG_CUDA(cudaMemsetAsync(h.sc.get(), 0, sizeof(Scalars), c.stream));
-  const int n0 = h.lv[0]->n_r;
+  const int n0 = h.lv[0]->B * h.lv[0]->n_r;
   h.x.alloc(n0); h.p.alloc(n0); h.q.alloc(n0); h.tmp.alloc(n0);
   h.r.alloc(n0); h.z.alloc(n0); h.zold.alloc(n0);
   RMG_CUDA(cudaHostAlloc(&h.pinned, 64 * sizeof(double), cudaHostAllocDefault));
@@ -442,7 +454,8 @@ void hier_build(Hier& h) {
       Lc.ncomp, Lc.c2r.get(), Lc.mask.get(), freeflag.get());
   RMG_LAUNCHED();
   h.nc = exclusive_scan(c, freeflag.get(), pos.get(), Lc.ncomp);
-  RMG_REQUIRE((long long)h.nc * h.nc < (1LL << 31), RMG_ERR_ARG,
+  const long long ncd = (long long)h.nc * Lc.B;
+  RMG_REQUIRE(ncd * ncd < (1LL << 31), RMG_ERR_ARG,
               "coarsest level too large for the dense solver (add levels)");
   h.cidx.alloc(Lc.ncomp);
   h.cu2slot.alloc(std::max(1, h.nc));
@@ -451,30 +464,35 @@ void hier_build(Hier& h) {
       Lc.ncomp, freeflag.get(), pos.get(), Lc.c2r.get(), h.cidx.get(), h.cu2slot.get(),
       h.cu2gid.get());
   RMG_LAUNCHED();
-  const size_t nc2 = (size_t)std::max(1, h.nc) * std::max(1, h.nc);
-  h.Mfac.alloc(nc2); h.X.alloc(nc2); h.Ainv.alloc(nc2);
-  h.xc.alloc(std::max(1, h.nc)); h.rc.alloc(std::max(1, h.nc));
+  const size_t nd = (size_t)std::max(1LL, ncd);
+  h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd);
+  h.xc.alloc(nd); h.rc.alloc(nd);
   RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
 }
 
+// D~^-1 = (Psi^T Psi diag([[A]]))^-1, per component of a block operator (diagonal of A_cc).
 static void compute_dinv(Hier& h, Level& L) {
   Ctx& c = *h.c;
   const int gb = persistent_grid(c, (L.n_r + 255) / 256);
-  double* y = h.v64[&L == h.lv[0] ? 0 : 0].y.get();
-  // use this level's own scratch
+  double* y = nullptr;
   for (int l = 0; l < h.levels(); ++l) if (h.lv[l] == &L) y = h.v64[l].y.get();
-  switch (L.kind) {
-    case 5: k_diag_local<5><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
-    case 7: k_diag_local<7><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
-    case 9: k_diag_local<9><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
-    default: k_diag_local<27><<<gb, 256, 0, c.stream>>>(L.n_r, L.coef.get(), L.mult.get(), L.dinv.get(), y); break;
-  }
-  RMG_LAUNCHED();
-  if (L.ngroups) {
-    k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
-        L.ngroups, L.gptr.get(), L.gslot.get(), y, EpiRecip{L.dinv.get()});
+  for (int b = 0; b < L.B; ++b) {
+    const double* cb = L.coef.get() + (size_t)(b * L.B + b) * L.kind * L.n_r;
+    double* db = L.dinv.get() + (size_t)b * L.n_r;
+    double* yb = y + (size_t)b * L.n_r;
+    switch (L.kind) {
+      case 5: k_diag_local<5><<<gb, 256, 0, c.stream>>>(L.n_r, cb, L.mult.get(), db, yb); break;
+      case 7: k_diag_local<7><<<gb, 256, 0, c.stream>>>(L.n_r, cb, L.mult.get(), db, yb); break;
+      case 9: k_diag_local<9><<<gb, 256, 0, c.stream>>>(L.n_r, cb, L.mult.get(), db, yb); break;
+      default: k_diag_local<27><<<gb, 256, 0, c.stream>>>(L.n_r, cb, L.mult.get(), db, yb); break;
+    }
     RMG_LAUNCHED();
+    if (L.ngroups) {
+      k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
+          L.ngroups, L.gptr.get(), L.gslot.get(), yb, EpiRecip{db});
+      RMG_LAUNCHED();
+    }
   }
 }
 
@@ -483,28 +501,34 @@ static void galerkin(Hier& h, int l, const Level& F, Level& C) {
   double* ap = h.layout->apbuf.get();
   const Grid Gf = F.grid(), Gc = C.grid();
   const int gf = persistent_grid(c, Gf.ntiles), gc = persistent_grid(c, Gc.ntiles);
+  // (P x I)^T A (P x I) of a B x B block operator is the scalar product on every block; a
+  // masked coarse row is the identity row in the diagonal blocks and zero elsewhere
+  for (int blk = 0; blk < F.B * F.B; ++blk) {
+  const double* fco = F.coef.get() + (size_t)blk * F.kind * F.n_r;
+  double* cco = C.coef.get() + (size_t)blk * C.kind * C.n_r;
+  const double mdiag = (blk / F.B == blk % F.B) ? 1.0 : 0.0;
 #define RMG_RAP(FK, CK, D)                                                                    \
   {                                                                                           \
     const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
     RMG_CUDA(cudaFuncSetAttribute(k_ap<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   smem));                                                     \
-    k_ap<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), F.mask.get(), \
+    k_ap<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, F.mask.get(),        \
                                                C.mask.get(), ap);                             \
   }                                                                                           \
   RMG_LAUNCHED();                                                                             \
   k_rtap<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, C.mask.get(),     \
-                                            C.mult.get(), C.coef.get())
+                                            C.mult.get(), mdiag, cco)
 #define RMG_RAPW(FK, CK, D)                                                                   \
   {                                                                                           \
     const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
     RMG_CUDA(cudaFuncSetAttribute(k_ap_w<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                   smem));                                                     \
-    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), F.coef.get(), h.pw[l].get(), \
+    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, h.pw[l].get(),       \
                                                  F.mask.get(), C.mask.get(), ap);             \
   }                                                                                           \
   RMG_LAUNCHED();                                                                             \
   k_rtap_w<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, h.pw[l].get(),   \
-                                              C.mask.get(), C.mult.get(), C.coef.get())
+                                              C.mask.get(), C.mult.get(), mdiag, cco)
   if (h.stored[l]) {
     switch (F.kind) {
       case 5: RMG_RAPW(5, 9, 2); break;
@@ -520,9 +544,10 @@ static void galerkin(Hier& h, int l, const Level& F, Level& C) {
       default: RMG_RAP(27, 27, 3); break;
     }
   }
+  RMG_LAUNCHED();
+  }
 #undef RMG_RAP
 #undef RMG_RAPW
-  RMG_LAUNCHED();
 }
 
 // Stored transfer weights for level -> level+1 (NULL restores linear interpolation). The
@@ -531,6 +556,8 @@ static void galerkin(Hier& h, int l, const Level& F, Level& C) {
 void set_transfer_weights(Hier& h, int level, const float* wr) {
   RMG_REQUIRE(level >= 0 && level + 1 < h.levels(), RMG_ERR_ARG,
               "transfer weights exist for levels 0 .. levels-2");
+  RMG_REQUIRE(h.lv[level]->B == 1 || !wr, RMG_ERR_ARG,
+              "stored transfer weights are for scalar operators");
   Level& L = *h.lv[level];
   if (!wr) {
     h.stored[level] = 0;
@@ -545,6 +572,7 @@ void set_transfer_weights(Hier& h, int level, const float* wr) {
 // Operator-dependent (series-resistance) weights of a level from its current operator.
 void opdep_weights(Hier& h, int level, float* wr) {
   RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
+  RMG_REQUIRE(h.lv[level]->B == 1, RMG_ERR_ARG, "operator-dependent weights are for scalar operators");
   Level& L = *h.lv[level];
   Ctx& c = *h.c;
   const Grid G = L.grid();
@@ -571,12 +599,12 @@ static void power_method(Hier& h, int l) {
   Level& L = *h.lv[l];
   cudaStream_t st = c.stream;
   LevelVecs<double>& V = h.v64[l];
-  const int n = L.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  const int n = L.B * L.n_r, eg = persistent_grid(c, (n + 255) / 256);
   Scalars* sc = h.sc.get();
-  k_power_init<<<eg, 256, 0, st>>>(n, L.gid.get(), L.mask.get(),
+  k_power_init<<<eg, 256, 0, st>>>(L.n_r, L.B, L.gid.get(), L.mask.get(),
                                    (unsigned long long)(h.o.power_seed_base + l), V.u.get());
   RMG_LAUNCHED();
-  dot(c, n, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
+  dot(c, n, L.n_r, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
   k_scale_div<<<eg, 256, 0, st>>>(n, V.u.get(), &sc->pw_norm, V.u.get());
   RMG_LAUNCHED();
   double* a = V.u.get();
@@ -588,8 +616,8 @@ static void power_method(Hier& h, int l) {
   }
   launch_stencil(c, L, L.coef.get(), a, V.y.get(), EpiScaled<double>{L.dinv.get(), b}, st,
                  nullptr);
-  dot(c, n, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
-  dot(c, n, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
+  dot(c, n, L.n_r, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
+  dot(c, n, L.n_r, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
   k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
   RMG_LAUNCHED();
 }
@@ -598,14 +626,15 @@ static void coarse_factor(Hier& h) {
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   Level& L = *h.lv[h.levels() - 1];
-  const int nc = h.nc;
-  if (nc == 0) return;
+  if (h.nc == 0) return;
+  const int nc = h.nc * L.B;     // dense dimension: B dofs per free composite node
   RMG_CUDA(cudaMemsetAsync(h.Mfac.get(), 0, (size_t)nc * nc * sizeof(double), st));
-  const int gb = persistent_grid(c, (L.ncomp + 127) / 128);
+  const dim3 gb(persistent_grid(c, (L.ncomp + 127) / 128), L.B);
 #define RMG_ASM(K)                                                                              \
-  k_coarse_assemble<K><<<gb, 128, 0, st>>>(L.ncomp, nc, L.regions.get(), L.nreg, L.n_r,         \
+  k_coarse_assemble<K><<<gb, 128, 0, st>>>(L.ncomp, L.B, L.regions.get(), L.nreg, L.n_r,        \
                                            L.coef.get(), L.gid.get(), h.cidx.get(), L.c2r.get(), \
-                                           L.cgrp.get(), L.gptr.get(), L.gslot.get(), h.Mfac.get())
+                                           L.cgrp.get(), L.gptr.get(), L.gslot.get(), nc,          \
+                                           h.Mfac.get())
   switch (L.kind) {
     case 5: RMG_ASM(5); break;
     case 7: RMG_ASM(7); break;
@@ -645,14 +674,15 @@ static void make_low_precision(Hier& h) {
   Ctx& c = *h.c;
   for (int l = 0; l < h.levels(); ++l) {
     Level& L = *h.lv[l];
-    const size_t nco = (size_t)L.kind * L.n_r;
+    const size_t nco = (size_t)L.B * L.B * L.kind * L.n_r;
     const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
     if (h.o.precision == RMG_PREC_FP32)
       k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
     else
       k_to_bf16<<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef16.get());
     RMG_LAUNCHED();
-    k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.n_r, L.dinv.get(), L.dinv32.get());
+    k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.B * L.n_r, L.dinv.get(),
+                                                      L.dinv32.get());
     RMG_LAUNCHED();
   }
 }
@@ -722,7 +752,7 @@ void vcycle(Hier& h) {
 void vcycle_apply(Hier& h, const double* r, double* z, int regional) {
   Ctx& c = *h.c;
   const Level& L0 = *h.lv[0];
-  const int n = L0.n_r, g = persistent_grid(c, (n + 255) / 256);
+  const int n = L0.B * L0.n_r, g = persistent_grid(c, (n + 255) / 256);
   double* b64 = h.v64[0].b.get();
   if (regional) k_copy<double><<<g, 256, 0, c.stream>>>(n, r, b64);
   else comp_to_reg(c, L0, r, b64, true);
@@ -762,16 +792,16 @@ double convergence_factor(Hier& h, int iters, unsigned long long seed) {
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   const Level& L0 = *h.lv[0];
-  const int n = L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  const int n = L0.B * L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
   Scalars* sc = h.sc.get();
   double* e = h.x.get();
   double* Ae = h.v64[0].b.get();      // the cycle's right-hand side buffer
   double* z = h.v64[0].u.get();
-  k_power_init<<<eg, 256, 0, st>>>(n, L0.gid.get(), L0.mask.get(), seed, e);
+  k_power_init<<<eg, 256, 0, st>>>(L0.n_r, L0.B, L0.gid.get(), L0.mask.get(), seed, e);
   RMG_LAUNCHED();
   auto anorm2 = [&]() {
     launch_stencil(c, L0, L0.coef.get(), e, h.v64[0].y.get(), EpiStore<double>{Ae}, st, nullptr);
-    dot(c, n, e, Ae, L0.mult.get(), &sc->pq, FIN_STORE, st);
+    dot(c, n, L0.n_r, e, Ae, L0.mult.get(), &sc->pq, FIN_STORE, st);
     RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->pq, sizeof(double), cudaMemcpyDeviceToHost, st));
     RMG_CUDA(cudaStreamSynchronize(st));
     return h.pinned[0];
@@ -802,7 +832,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   const Level& L0 = *h.lv[0];
-  const int n = L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  const int n = L0.B * L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
   const int dg = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
   Scalars* sc = h.sc.get();
   const bool mixed = h.mixed();
@@ -815,8 +845,8 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   // r = b - A x
   launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
                  EpiResid<double>{breg, rvec}, st, nullptr);
-  dot(c, n, breg, breg, L0.mult.get(), &sc->bb, FIN_STORE, st);
-  dot(c, n, rvec, rvec, L0.mult.get(), &sc->rr, FIN_STORE, st);
+  dot(c, n, L0.n_r, breg, breg, L0.mult.get(), &sc->bb, FIN_STORE, st);
+  dot(c, n, L0.n_r, rvec, rvec, L0.mult.get(), &sc->rr, FIN_STORE, st);
   auto read2 = [&](double* a, double* bb) {
     RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
     RMG_CUDA(cudaMemcpyAsync(h.pinned + 1, &sc->bb, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -846,7 +876,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   int status_conv = 0;
   if (relres > rtol && bnorm > 0) {
     precondition();
-    dot(c, n, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
+    dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
     k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.p.get());
     RMG_LAUNCHED();
     if (mixed) {
@@ -856,11 +886,11 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
     for (it = 1; it <= maxit; ++it) {
       launch_stencil(c, L0, L0.coef.get(), h.p.get(), h.v64[0].y.get(),
                      EpiStore<double>{h.q.get()}, st, nullptr);
-      dot(c, n, h.p.get(), h.q.get(), L0.mult.get(), &sc->pq, FIN_STORE, st);
+      dot(c, n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), &sc->pq, FIN_STORE, st);
       k_alpha<<<1, 1, 0, st>>>(sc);
       RMG_LAUNCHED();
-      k_cg_update<<<dg, 256, 0, st>>>(n, h.p.get(), h.q.get(), L0.mult.get(), sc, h.x.get(), rvec,
-                                     c.partials.get());
+      k_cg_update<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc, h.x.get(),
+                                     rvec, c.partials.get());
       RMG_LAUNCHED();
       k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rr, FIN_STORE);
       RMG_LAUNCHED();
@@ -869,9 +899,9 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       if (history) history[it] = relres;
       if (relres <= rtol) { status_conv = 1; break; }
       precondition();
-      dot(c, n, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
+      dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
       if (mixed) {
-        dot(c, n, rvec, h.zold.get(), L0.mult.get(), &sc->beta, FIN_STORE, st);
+        dot(c, n, L0.n_r, rvec, h.zold.get(), L0.mult.get(), &sc->beta, FIN_STORE, st);
         k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
         RMG_LAUNCHED();
       }
@@ -888,7 +918,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   // true residual from the final iterate
   launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
                  EpiResid<double>{breg, h.q.get()}, st, nullptr);
-  dot(c, n, h.q.get(), h.q.get(), L0.mult.get(), &sc->rr, FIN_STORE, st);
+  dot(c, n, L0.n_r, h.q.get(), h.q.get(), L0.mult.get(), &sc->rr, FIN_STORE, st);
   double rtrue = 0;
   read2(&rtrue, &bb);
   const auto t1 = std::chrono::steady_clock::now();

@@ -154,7 +154,8 @@ struct Ctx;
 // One level of the regional hierarchy.
 struct Level {
   int dim = 3;
-  int kind = 7;                  // stencil points stored per node
+  int kind = 7;                  // stencil points stored per node (per block)
+  int B = 1;                     // dofs per node (3 for elasticity): B x B blocks of stencils
   int nreg = 0;
   std::vector<int> hdims;        // 3 per region
   std::vector<int> hoff;         // nreg + 1

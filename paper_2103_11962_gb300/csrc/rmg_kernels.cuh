@@ -103,6 +103,66 @@ k_groups(int ngroups, const int* __restrict__ gptr, const int* __restrict__ gslo
   }
 }
 
+// ---- block operators (B dofs per node; elasticity: B = 3) ---------------------------------
+// Coefficients of block (c, c') are a scalar stencil: coef[((c * B + c') * S + s) * n_r + n];
+// vectors are component-major: v[c * n_r + n]. The epilogues receive the flat index c * n_r + n.
+template <int KIND, int B, typename CT, typename VT, typename AT, class Epi>
+__global__ void __launch_bounds__(kTile)
+k_bstencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
+           const uint8_t* __restrict__ mult, AT* __restrict__ y, Epi epi) {
+  using S = Sten<KIND>;
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    decode(li, R, i, j, l);
+    AT au[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) au[c] = AT(0);
+    const int sy = R.nx, sz = R.nx * R.ny;
+#pragma unroll
+    for (int s = 0; s < S::S; ++s) {
+      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+      bool ok = true;
+      if (dx < 0) ok &= (i > 0);
+      if (dx > 0) ok &= (i < R.nx - 1);
+      if (dy < 0) ok &= (j > 0);
+      if (dy > 0) ok &= (j < R.ny - 1);
+      if (dz < 0) ok &= (l > 0);
+      if (dz > 0) ok &= (l < R.nz - 1);
+      if (!ok) continue;
+      const int nb = n + dx + dy * sy + dz * sz;
+      AT uv[B];
+#pragma unroll
+      for (int c2 = 0; c2 < B; ++c2) uv[c2] = AT(u[(size_t)c2 * G.n_r + nb]);
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+#pragma unroll
+        for (int c2 = 0; c2 < B; ++c2)
+          au[c] = fma(AT(coef[((size_t)(c * B + c2) * S::S + s) * G.n_r + n]), uv[c2], au[c]);
+    }
+    if (mult[n] > 1) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) y[(size_t)c * G.n_r + n] = au[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < B; ++c) epi(c * G.n_r + n, au[c], 1);
+    }
+  RMG_END_FOR_NODES
+}
+
+template <typename AT, class Epi>
+__global__ void __launch_bounds__(256)
+k_groups_b(int ngroups, int B, int n_r, const int* __restrict__ gptr,
+           const int* __restrict__ gslot, const AT* __restrict__ y, Epi epi) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+    const int a = gptr[g], e = gptr[g + 1];
+    for (int c = 0; c < B; ++c) {
+      AT s = AT(0);
+      for (int k = a; k < e; ++k) s += y[(size_t)c * n_r + gslot[k]];
+      for (int k = a; k < e; ++k) epi(c * n_r + gslot[k], s, e - a);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ epilogues
 // An epilogue receives the node, the composite row result (A u)_n and the multiplicity m of
 // the node (1 in phase A, the group size in phase B).
@@ -410,13 +470,14 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // Composite inner product of consistent regional vectors: sum x y / mult.
+// n = B * n_nodes entries, component-major; the multiplicity is that of the node k mod n_nodes.
 template <typename XT, typename YT>
 __global__ void __launch_bounds__(256)
-k_dot(int n, const XT* __restrict__ x, const YT* __restrict__ y, const uint8_t* __restrict__ mult,
-      double* __restrict__ partials) {
+k_dot(int n, int n_nodes, const XT* __restrict__ x, const YT* __restrict__ y,
+      const uint8_t* __restrict__ mult, double* __restrict__ partials) {
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    s += (double(x[k]) * double(y[k])) * inv_mult<double>(mult[k]);
+    s += (double(x[k]) * double(y[k])) * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }

@@ -1,0 +1,46 @@
+// Launch helper shared by the translation units: phase A (region stencils, scalar or B x B
+// blocks) and phase B (interface groups) with one epilogue.
+#pragma once
+
+#include "rmg_kernels.cuh"
+
+namespace rmg {
+
+template <class Epi, typename CT, typename VT, typename AT>
+void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
+                    cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
+                    cudaEvent_t ev1 = nullptr) {
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+  // external record nodes when capturing, so the events can be timed after a graph replay
+  if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));
+  if (L.B == 1) {
+    switch (L.kind) {
+      case 5: k_stencil<5, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+      case 7: k_stencil<7, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+      case 9: k_stencil<9, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+      default: k_stencil<27, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
+    }
+  } else {
+    RMG_REQUIRE(L.B == 3 && (L.kind == 27 || L.kind == 9), RMG_ERR_ARG,
+                "block operators need 3 dofs per node and a 27- or 9-point stencil");
+    if (L.kind == 27)
+      k_bstencil<27, 3, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi);
+    else
+      k_bstencil<9, 3, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi);
+  }
+  RMG_LAUNCHED();
+  if (ev1) RMG_CUDA(cudaEventRecordWithFlags(ev1, st, g_capturing ? cudaEventRecordExternal : 0));
+  if (launches) ++*launches;
+  if (L.ngroups) {
+    const int gg = persistent_grid(c, (L.ngroups + 255) / 256);
+    if (L.B == 1)
+      k_groups<AT><<<gg, 256, 0, st>>>(L.ngroups, L.gptr.get(), L.gslot.get(), y, epi);
+    else
+      k_groups_b<AT><<<gg, 256, 0, st>>>(L.ngroups, L.B, L.n_r, L.gptr.get(), L.gslot.get(), y, epi);
+    RMG_LAUNCHED();
+    if (launches) ++*launches;
+  }
+}
+
+}  // namespace rmg

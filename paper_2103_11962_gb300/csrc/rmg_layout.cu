@@ -3,6 +3,7 @@
 #include <climits>
 
 #include "rmg_kernels.cuh"
+#include "rmg_launch.cuh"
 #include "rmg_layout.cuh"
 
 namespace rmg {
@@ -323,8 +324,10 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
             const int* __restrict__ c2r, const int* __restrict__ cgrp,
             const int* __restrict__ gptr, const int* __restrict__ gslot,
             const int64_t* __restrict__ rowptr, const int64_t* __restrict__ col,
-            const double* __restrict__ val, int ncomp, double* __restrict__ coef, int* err) {
+            const double* __restrict__ val, int ncomp, int B, double* __restrict__ coef, int* err) {
   using S = Sten<KIND>;
+  // block (c, cp) of a B-dof operator: rows g*B + c, columns g'*B + cp (blockIdx.y = c*B + cp)
+  const int c_row = blockIdx.y / B, c_col = blockIdx.y % B;
   RMG_FOR_NODES(G)
     int i, j, l;
     decode(li, R, i, j, l);
@@ -334,11 +337,13 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
 #pragma unroll
     for (int s = 0; s < S::S; ++s) acc[s] = 0.0;
     double zsum = 0.0, offsum = 0.0;
-    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+    const int64_t row = (int64_t)g * B + c_row;
+    for (int64_t e = rowptr[row]; e < rowptr[row + 1]; ++e) {
       const int64_t c64 = col[e];
       const double v = val[e];
-      if (c64 < 0 || c64 >= ncomp) { set_err(err, DERR_GID_RANGE); continue; }
-      const int c = (int)c64;
+      if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); continue; }
+      if (c64 % B != c_col) continue;
+      const int c = (int)(c64 / B);
       zsum += v;
       if (c == g) continue;
       const int sc = copy_in_region(c, R, nodes, c2r, cgrp, gptr, gslot);
@@ -355,51 +360,56 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
         if (s == slot) acc[s] += vs;
     }
     acc[S::CENTER] = zsum * inv_mult<double>(mult[n]) - offsum;
+    double* cb = coef + (size_t)blockIdx.y * S::S * G.n_r;
 #pragma unroll
-    for (int s = 0; s < S::S; ++s) coef[(size_t)s * G.n_r + n] = acc[s];
+    for (int s = 0; s < S::S; ++s) cb[(size_t)s * G.n_r + n] = acc[s];
   RMG_END_FOR_NODES
 }
 
-__global__ void k_comp_to_reg(int n_r, const int* __restrict__ gid, const double* __restrict__ c,
+// Composite vectors with B dofs per node are node-major (dof g*B + c); regional vectors are
+// component-major (c * n_r + n).
+__global__ void k_comp_to_reg(int n_r, int B, const int* __restrict__ gid,
+                              const uint8_t* __restrict__ mask, const double* __restrict__ c,
                               double* __restrict__ r) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
-    r[k] = c[gid[k]];
+    for (int b = 0; b < B; ++b)
+      r[(size_t)b * n_r + k] = (mask && mask[k]) ? 0.0 : c[(size_t)gid[k] * B + b];
 }
 
-__global__ void k_comp_to_reg_masked(int n_r, const int* __restrict__ gid,
-                                     const uint8_t* __restrict__ mask,
-                                     const double* __restrict__ c, double* __restrict__ r) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
-    r[k] = mask[k] ? 0.0 : c[gid[k]];
-}
-
-__global__ void k_reg_to_comp(int ncomp, const int* __restrict__ c2r, const int* __restrict__ cgrp,
-                              const int* __restrict__ gptr, const int* __restrict__ gslot,
-                              const double* __restrict__ r, double* __restrict__ c, int average) {
+__global__ void k_reg_to_comp(int ncomp, int n_r, int B, const int* __restrict__ c2r,
+                              const int* __restrict__ cgrp, const int* __restrict__ gptr,
+                              const int* __restrict__ gslot, const double* __restrict__ r,
+                              double* __restrict__ c, int average) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncomp; g += gridDim.x * blockDim.x) {
     const int grp = cgrp[g];
-    if (grp < 0) { c[g] = r[c2r[g]]; continue; }
-    double s = 0.0;
-    const int a = gptr[grp], e = gptr[grp + 1];
-    for (int q = a; q < e; ++q) s += r[gslot[q]];
-    c[g] = average ? s / (double)(e - a) : s;
+    for (int b = 0; b < B; ++b) {
+      const double* rb = r + (size_t)b * n_r;
+      if (grp < 0) { c[(size_t)g * B + b] = rb[c2r[g]]; continue; }
+      double s = 0.0;
+      const int a = gptr[grp], e = gptr[grp + 1];
+      for (int q = a; q < e; ++q) s += rb[gslot[q]];
+      c[(size_t)g * B + b] = average ? s / (double)(e - a) : s;
+    }
   }
 }
 }  // namespace
 
-void split_from_csr(Ctx& c, Level& L, int kind, const int64_t* rowptr, const int64_t* col,
+void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, const int64_t* col,
                     const double* val) {
   RMG_REQUIRE(rowptr && col && val, RMG_ERR_ARG, "CSR arrays are required");
   RMG_REQUIRE((L.dim == 2 && (kind == 5 || kind == 9)) || (L.dim == 3 && (kind == 7 || kind == 27)),
               RMG_ERR_ARG, "stencil must be 5/9 in 2D and 7/27 in 3D");
+  RMG_REQUIRE(B == 1 || (B == 3 && (kind == 27 || kind == 9)), RMG_ERR_ARG,
+              "block operators need 3 dofs per node and a 27- or 9-point stencil");
   L.kind = kind;
-  L.coef.ensure((size_t)kind * L.n_r);
+  L.B = B;
+  L.coef.ensure((size_t)B * B * kind * L.n_r);
   const Grid G = L.grid();
-  const int gb = persistent_grid(c, G.ntiles);
+  const dim3 gb(persistent_grid(c, G.ntiles), B * B);
 #define RMG_SPLIT(K)                                                                        \
   k_split_csr<K><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(),     \
                                              L.cgrp.get(), L.gptr.get(), L.gslot.get(),      \
-                                             rowptr, col, val, L.ncomp, L.coef.get(),    \
+                                             rowptr, col, val, L.ncomp, B, L.coef.get(), \
                                              c.d_err.get())
   switch (kind) {
     case 5: RMG_SPLIT(5); break;
@@ -414,40 +424,21 @@ void split_from_csr(Ctx& c, Level& L, int kind, const int64_t* rowptr, const int
 
 void comp_to_reg(Ctx& c, const Level& L, const double* comp, double* reg, bool zero_masked) {
   const int gb = persistent_grid(c, (L.n_r + 255) / 256);
-  if (zero_masked)
-    k_comp_to_reg_masked<<<gb, 256, 0, c.stream>>>(L.n_r, L.gid.get(), L.mask.get(), comp, reg);
-  else
-    k_comp_to_reg<<<gb, 256, 0, c.stream>>>(L.n_r, L.gid.get(), comp, reg);
+  k_comp_to_reg<<<gb, 256, 0, c.stream>>>(L.n_r, L.B, L.gid.get(),
+                                          zero_masked ? L.mask.get() : nullptr, comp, reg);
   RMG_LAUNCHED();
 }
 
 void reg_to_comp(Ctx& c, const Level& L, const double* reg, double* comp, int average) {
   k_reg_to_comp<<<persistent_grid(c, (L.ncomp + 255) / 256), 256, 0, c.stream>>>(
-      L.ncomp, L.c2r.get(), L.cgrp.get(), L.gptr.get(), L.gslot.get(), reg, comp, average);
+      L.ncomp, L.n_r, L.B, L.c2r.get(), L.cgrp.get(), L.gptr.get(), L.gslot.get(), reg, comp,
+      average);
   RMG_LAUNCHED();
 }
 
 // y = Psi^T Psi [[A]] u in FP64 with the level's FP64 coefficients.
 void regional_apply(Ctx& c, const Level& L, const double* u, double* y, double* ypart) {
-  const Grid G = L.grid();
-  const int gb = persistent_grid(c, G.ntiles);
-  EpiStore<double> epi{y};
-#define RMG_APPLY(K)                                                                       \
-  k_stencil<K, double, double, double><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), u,      \
-                                                                   L.mult.get(), ypart, epi)
-  switch (L.kind) {
-    case 5: RMG_APPLY(5); break;
-    case 7: RMG_APPLY(7); break;
-    case 9: RMG_APPLY(9); break;
-    default: RMG_APPLY(27); break;
-  }
-#undef RMG_APPLY
-  RMG_LAUNCHED();
-  if (L.ngroups) {
-    k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
-        L.ngroups, L.gptr.get(), L.gslot.get(), ypart, epi);
-    RMG_LAUNCHED();
-  }
+  launch_stencil(c, L, L.coef.get(), u, ypart, EpiStore<double>{y}, c.stream, nullptr);
 }
 
 }  // namespace rmg

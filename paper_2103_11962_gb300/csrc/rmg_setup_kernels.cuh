@@ -171,7 +171,7 @@ __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r
 template <int CK, int DIM>
 __global__ void __launch_bounds__(kTile)
 k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
-       const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult,
+       const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult, double mdiag,
        double* __restrict__ ccoef) {
   using CS = Sten<CK>;
   RMG_FOR_NODES(Gc)
@@ -179,7 +179,7 @@ k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ 
 #pragma unroll
     for (int o = 0; o < 27; ++o) acc[o] = 0.0;
     if (cmask[n]) {
-      acc[DIM == 3 ? 13 : 4] = 1.0 / (double)cmult[n];
+      acc[DIM == 3 ? 13 : 4] = mdiag / (double)cmult[n];
     } else {
       int I, J, L;
       decode(li, R, I, J, L);
@@ -247,14 +247,14 @@ template <int CK, int DIM>
 __global__ void __launch_bounds__(kTile)
 k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
          const float* __restrict__ wr, const uint8_t* __restrict__ cmask,
-         const uint8_t* __restrict__ cmult, double* __restrict__ ccoef) {
+         const uint8_t* __restrict__ cmult, double mdiag, double* __restrict__ ccoef) {
   using CS = Sten<CK>;
   RMG_FOR_NODES(Gc)
     double acc[27];
 #pragma unroll
     for (int o = 0; o < 27; ++o) acc[o] = 0.0;
     if (cmask[n]) {
-      acc[DIM == 3 ? 13 : 4] = 1.0 / (double)cmult[n];
+      acc[DIM == 3 ? 13 : 4] = mdiag / (double)cmult[n];
     } else {
       int I, J, L;
       decode(li, R, I, J, L);
@@ -326,10 +326,15 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
   return (double)(z >> 11) * 0x1.0p-52 - 1.0;
 }
 
-__global__ void k_power_init(int n_r, const int* __restrict__ gid, const uint8_t* __restrict__ mask,
-                             unsigned long long seed, double* __restrict__ x) {
+// Random start vector: value of composite dof g*B + b (dofs numbered node-major) at every
+// copy of the node; zero at masked nodes. Regional vectors are component-major.
+__global__ void k_power_init(int n_r, int B, const int* __restrict__ gid,
+                             const uint8_t* __restrict__ mask, unsigned long long seed,
+                             double* __restrict__ x) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
-    x[k] = mask[k] ? 0.0 : splitmix_pm1(seed, (unsigned long long)gid[k]);
+    for (int b = 0; b < B; ++b)
+      x[(size_t)b * n_r + k] =
+          mask[k] ? 0.0 : splitmix_pm1(seed, (unsigned long long)gid[k] * B + b);
 }
 
 // out = sum of partials, then an operation on the scalar block.
@@ -402,18 +407,21 @@ __global__ void k_coarse_maps(int ncomp, const int* __restrict__ freeflag, const
 }
 
 // Abar = Psibar [[Abar]] Psibar^T restricted to unmasked nodes (eq. CoarseCompositeOperator):
-// row of composite node g = sum over its regional copies of their region rows.
+// row of composite node g = sum over its regional copies of their region rows. With B dofs per
+// node the dense matrix has dimension B * nc, dof cidx * B + b (blockIdx.y = row component).
 template <int KIND>
-__global__ void k_coarse_assemble(int ncomp, int nc, const RegionDev* __restrict__ regs, int nreg,
+__global__ void k_coarse_assemble(int ncomp, int B, const RegionDev* __restrict__ regs, int nreg,
                                   int n_r, const double* __restrict__ coef,
                                   const int* __restrict__ gid, const int* __restrict__ cidx,
                                   const int* __restrict__ c2r, const int* __restrict__ cgrp,
                                   const int* __restrict__ gptr, const int* __restrict__ gslot,
-                                  double* __restrict__ M) {
+                                  int nd, double* __restrict__ M) {
   using S = Sten<KIND>;
+  const int b = blockIdx.y;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ncomp; g += gridDim.x * blockDim.x) {
-    const int row = cidx[g];
-    if (row < 0) continue;
+    const int rowc = cidx[g];
+    if (rowc < 0) continue;
+    const size_t row = (size_t)rowc * B + b;
     const int grp = cgrp[g];
     const int a = grp < 0 ? 0 : gptr[grp];
     const int e = grp < 0 ? 1 : gptr[grp + 1];
@@ -428,7 +436,9 @@ __global__ void k_coarse_assemble(int ncomp, int nc, const RegionDev* __restrict
         const int n2 = R.off + x + R.nx * (y + R.ny * z);
         const int col = cidx[gid[n2]];
         if (col < 0) continue;
-        M[(size_t)row * nc + col] += coef[(size_t)s * n_r + n];
+        for (int b2 = 0; b2 < B; ++b2)
+          M[row * nd + (size_t)col * B + b2] +=
+              coef[((size_t)(b * B + b2) * S::S + s) * n_r + n];
       }
     }
   }

@@ -71,6 +71,8 @@ def lib():
         "rmg_layout_sizes": (ctypes.c_int, [P, I64P, I64P, I64P, I64P]),
         "rmg_operator_from_csr": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "rmg_operator_from_region_stencils": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "rmg_operator_from_block_csr": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P]),
+        "rmg_hier_dofs_per_node": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_regional_apply": (ctypes.c_int, [P, P, P]),
         "rmg_comp_to_reg": (ctypes.c_int, [P, P, P]),
         "rmg_reg_to_comp": (ctypes.c_int, [P, P, P, ctypes.c_int]),
@@ -125,6 +127,7 @@ def exported_symbols():
             "rmg_hier_level_export", "rmg_hier_lambda", "rmg_hier_coarse_matrix",
             "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
+            "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
             "rmg_hier_opdep_weights", "rmg_hier_convergence_factor", "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
             "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
@@ -225,6 +228,10 @@ class Layout:
                                                    _ptr(val)))
         self._csr = None
 
+    def operator_from_block_csr(self, stencil, dofs_per_node, rowptr, col, val):
+        self.ctx.check(lib().rmg_operator_from_block_csr(self.h, stencil, dofs_per_node,
+                                                         _ptr(rowptr), _ptr(col), _ptr(val)))
+
     def operator_from_region_stencils(self, stencil, coeffs):
         self.ctx.check(lib().rmg_operator_from_region_stencils(self.h, stencil, _ptr(coeffs)))
 
@@ -286,6 +293,11 @@ class Hierarchy:
                                                   ctypes.byref(s)))
         return a.value, b.value, s.value
 
+    def dofs_per_node(self):
+        v = ctypes.c_int()
+        self.ctx.check(lib().rmg_hier_dofs_per_node(self.h, ctypes.byref(v)))
+        return v.value
+
     def level_export(self, level, coeffs=None, dinv=None, gids=None):
         self.ctx.check(lib().rmg_hier_level_export(self.h, level, _ptr(coeffs), _ptr(dinv),
                                                    _ptr(gids)))
@@ -299,7 +311,8 @@ class Hierarchy:
         nc = ctypes.c_int64()
         self.ctx.check(lib().rmg_hier_coarse_matrix(self.h, ctypes.byref(nc), None, None))
         n = nc.value
-        dense = np.zeros((n, n))
+        B = self.dofs_per_node()
+        dense = np.zeros((n * B, n * B))
         ids = np.zeros(n, dtype=np.int64)
         if n:
             self.ctx.check(lib().rmg_hier_coarse_matrix(self.h, ctypes.byref(nc),

@@ -590,3 +590,58 @@ def test_bf16_rounding_matches_definition():
     assert out[2] == 1.0 + 2 ** -6          # tie between 1+2^-7 and 1+2^-6: even mantissa
     assert out[3] == 1.0
     assert out[4] == -2.5
+
+
+# ---------------------------------------------------------------------------- elasticity (3 dofs)
+def test_elasticity_element_rigid_body_modes():
+    """The Q1 elasticity element annihilates the six rigid-body motions and is symmetric."""
+    K = W.q1_element_elasticity(0.1, 2.0, 0.3)
+    assert abs(K - K.T).max() < 1e-15
+    corners = np.array([[(a >> 0) & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float) * 0.1
+    modes = []
+    for c in range(3):
+        t = np.zeros(24); t[c::3] = 1.0; modes.append(t)
+    for (i, j) in [(0, 1), (1, 2), (0, 2)]:
+        r = np.zeros(24); r[i::3] = -corners[:, j]; r[j::3] = corners[:, i]; modes.append(r)
+    for m in modes:
+        assert abs(K @ m).max() < 1e-14
+    w = np.linalg.eigvalsh(K)
+    assert np.sum(w < 1e-12 * w.max()) == 6          # exactly the rigid-body modes
+
+
+@pytest.fixture(scope="module")
+def el3d():
+    return W.elasticity3d(region_grid=(2, 2, 1), choices=(10,), seed=4)
+
+
+def test_elasticity_block_split_and_apply(el3d):
+    p = el3d
+    levels = hierarchy.build_block(p, 2)
+    L0 = levels[0].layout
+    assert abs(L0.Psi @ levels[0].Ar @ L0.Psi.T - levels[0].A).max() <= 1e-15 * abs(levels[0].A).max() * 4
+    x = np.random.default_rng(1).standard_normal(3 * p.n_nodes)
+    lhs = L0.interface_sum(levels[0].Ar @ L0.to_regional(x))
+    rhs = L0.to_regional(levels[0].A @ x)
+    assert np.abs(lhs - rhs).max() <= 1e-14 * np.abs(rhs).max()
+    # the Galerkin theorem with I (x) P
+    f, c = levels
+    Psib = c.layout.Psi
+    lhs = Psib @ (f.Pr.T @ f.Ar @ f.Pr) @ Psib.T
+    rhs = f.P.T @ f.A @ f.P
+    assert abs(lhs - rhs).max() <= 1e-13 * abs(rhs).max()
+
+
+def test_elasticity_regional_cycle_equals_composite(el3d):
+    p = el3d
+    levels = hierarchy.build_block(p, 2)
+    o = cycle.Options(smoother="chebyshev", nu1=1, nu2=1, degree=3)
+    cm, rm = cycle.CompositeMG(levels, o), cycle.RegionalMG(levels, o)
+    perm = hierarchy.node_major_to_component_major(p.n_nodes, 3)
+    b = p.b[perm]
+    L0 = levels[0].layout
+    uc = cm.precondition(b)
+    ur = L0.average_to_composite(rm.precondition(L0.to_regional(b)))
+    assert np.abs(uc - ur).max() <= 1e-12 * np.abs(uc).max()
+    x, it, _ = krylov.pcg(levels[0].A, b, krylov.regional_preconditioner(rm), rtol=1e-12)
+    xd = sp.linalg.spsolve(levels[0].A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)

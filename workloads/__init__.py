@@ -387,3 +387,113 @@ def config(name: str, **kw) -> Problem:
         return highcontrast3d_7pt(**{"region_grid": (7, 7, 7), "choices": (28, 55, 82),
                                      "seed": 3, **kw})
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------------------
+# linear elasticity (3 dofs per node)
+
+def q1_element_elasticity(h=1.0, E=1.0, nu=0.3):
+    """24x24 stiffness of the trilinear hexahedron [0,h]^3 for isotropic linear elasticity
+    (2x2x2 Gauss quadrature). Dofs are node-major: 3 a + c for local node a, component c;
+    local node a has corner offsets (a & 1, (a >> 1) & 1, (a >> 2) & 1)."""
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2 * mu
+    D[3, 3] = D[4, 4] = D[5, 5] = mu
+    g = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+    corners = np.array([[(a >> 0) & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float)
+    K = np.zeros((24, 24))
+    for qz in g:
+        for qy in g:
+            for qx in g:
+                xi = (np.array([qx, qy, qz]) + 1.0) / 2.0
+                Bm = np.zeros((6, 24))
+                for a in range(8):
+                    c = corners[a]
+                    f = [xi[d] if c[d] else 1.0 - xi[d] for d in range(3)]
+                    df = [1.0 if c[d] else -1.0 for d in range(3)]
+                    dx, dy, dz = (np.array([df[0] * f[1] * f[2], f[0] * df[1] * f[2],
+                                            f[0] * f[1] * df[2]]) / h)
+                    Bm[0, 3 * a] = dx
+                    Bm[1, 3 * a + 1] = dy
+                    Bm[2, 3 * a + 2] = dz
+                    Bm[3, 3 * a], Bm[3, 3 * a + 1] = dy, dx
+                    Bm[4, 3 * a + 1], Bm[4, 3 * a + 2] = dz, dy
+                    Bm[5, 3 * a], Bm[5, 3 * a + 2] = dz, dx
+                K += Bm.T @ D @ Bm * (h ** 3 / 8.0)
+    return K
+
+
+def _csr_from_block_stencil(global_dims, offsets, values, mask, B):
+    """CSR (dofs node-major, g * B + c) from per-node B x B block stencils values[s, c, c']."""
+    Nx, Ny, Nz = global_dims
+    n = Nx * Ny * Nz
+    S = len(offsets)
+    z, y, x = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    maskg = mask.reshape(Nz, Ny, Nx).astype(bool)
+    cols = np.empty((n, B, S, B), dtype=np.int64)
+    vals = np.empty((n, B, S, B), dtype=np.float64)
+    keep = np.empty((n, B, S, B), dtype=bool)
+    for s, (dx, dy, dz) in enumerate(offsets):
+        xx, yy, zz = x + dx, y + dy, z + dz
+        inside = (xx >= 0) & (xx < Nx) & (yy >= 0) & (yy < Ny) & (zz >= 0) & (zz < Nz)
+        g = np.where(inside, xx + Nx * (yy + Ny * zz), 0)
+        centre = (dx, dy, dz) == (0, 0, 0)
+        nb_masked = np.zeros_like(inside)
+        nb_masked[inside] = maskg.reshape(-1)[g[inside]]
+        for c in range(B):
+            for c2 in range(B):
+                v = np.where(inside, values[s, c, c2], 0.0)
+                if centre:
+                    v = np.where(maskg, 1.0 if c == c2 else 0.0, v)
+                    k = (~maskg) | (c == c2)
+                    k = k & ((v != 0.0) | (c == c2))
+                else:
+                    k = inside & ~maskg & ~nb_masked & (v != 0.0)
+                cols[:, c, s, c2] = (g * B + c2).reshape(-1)
+                vals[:, c, s, c2] = v.reshape(-1)
+                keep[:, c, s, c2] = k.reshape(-1)
+    cols = cols.reshape(n * B, S * B)
+    vals = vals.reshape(n * B, S * B)
+    keep = keep.reshape(n * B, S * B)
+    rowptr = np.zeros(n * B + 1, dtype=np.int64)
+    np.cumsum(keep.sum(axis=1), out=rowptr[1:])
+    A = sp.csr_matrix((vals[keep], cols[keep], rowptr), shape=(n * B, n * B))
+    A.sort_indices()
+    return A
+
+
+def elasticity3d(region_grid=(3, 3, 3), choices=(28,), seed=4, sigma=0.5, nu=0.3, rhs=True,
+                 load=(0.0, 0.0, -1.0)):
+    """3D linear elasticity, trilinear hexahedra, 3 dofs per node, Young's modulus
+    E = exp(N(0, sigma^2)) per element, Poisson ratio nu, the x = 0 face clamped, uniform body
+    load lumped to the nodes (h^3 per node)."""
+    rng = np.random.default_rng(seed)
+    slabs = tuple(tuple(int(v) for v in rng.choice(np.asarray(choices), size=k))
+                  for k in region_grid)
+    gdims, rdims, gids = region_map(slabs)
+    Nx, Ny, Nz = gdims
+    h = 1.0 / (Nx - 1)
+    E = np.exp(sigma * rng.standard_normal(size=(Nz - 1, Ny - 1, Nx - 1)))
+    Ke = q1_element_elasticity(h, 1.0, nu)
+    corners = [((a >> 0) & 1, (a >> 1) & 1, (a >> 2) & 1) for a in range(8)]
+    vals = np.zeros((27, 3, 3, Nz, Ny, Nx))
+    for a, (ax, ay, az) in enumerate(corners):
+        for c, (cx, cy, cz) in enumerate(corners):
+            s = (cx - ax + 1) + 3 * (cy - ay + 1) + 9 * (cz - az + 1)
+            blk = Ke[3 * a:3 * a + 3, 3 * c:3 * c + 3]
+            for i in range(3):
+                for j in range(3):
+                    vals[s, i, j, az:az + Nz - 1, ay:ay + Ny - 1, ax:ax + Nx - 1] += blk[i, j] * E
+    mask = boundary_mask(gdims, faces=("x0",))
+    A = _csr_from_block_stencil(gdims, OFFS27, vals, mask, 3)
+    n = Nx * Ny * Nz
+    b = np.zeros(3 * n)
+    if rhs:
+        b.reshape(n, 3)[:] = np.asarray(load) * h ** 3
+        b.reshape(n, 3)[mask.astype(bool)] = 0.0
+    return Problem("elasticity3d", 3, 3, gdims, slabs, rdims, gids, mask, A, b, 27,
+                   dict(seed=seed, region_grid=tuple(region_grid), choices=tuple(choices),
+                        sigma=sigma, nu=nu))
