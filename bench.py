@@ -33,10 +33,18 @@ RTOL = 1e-10
 # Per-node algorithmic bytes and FP64 flops of the timed kernel, the fine-level Chebyshev
 # recurrence sweep with a 7-point stencil (k_stencil<7, EpiCheb>): 7 coefficients, u, b,
 # D~^-1, d read; d and u_out written; 1-byte multiplicity read.
-SWEEP_BYTES = {("fp64", 7): 7 * 8 + 4 * 8 + 2 * 8 + 1,
-               ("fp32", 7): 7 * 4 + 4 * 4 + 2 * 4 + 1,
-               ("bf16", 7): 7 * 2 + 4 * 4 + 2 * 4 + 1}
-SWEEP_FLOPS = {7: 2 * 7 + 6}
+def sweep_bytes(prec, stencil, B=1):
+    """Algorithmic bytes per regional node of the Chebyshev recurrence sweep: B*B*S stencil
+    coefficients, u, b, D~^-1 and d read and d, u_out written for each of the B components,
+    and the 1-byte multiplicity."""
+    cb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    vb = 8 if prec == "fp64" else 4
+    return B * B * stencil * cb + B * 6 * vb + 1
+
+
+def sweep_flops(stencil, B=1):
+    """FP64 flops per regional node of the same sweep (2 per stored coefficient + 6 per dof)."""
+    return 2 * B * B * stencil + 6 * B
 
 WORKLOADS = {
     "c2_diffusion3d": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
@@ -45,6 +53,18 @@ WORKLOADS = {
                                 "per-element kappa (sigma 1), Chebyshev degree 3, 4 levels"),
     "c2_quarter": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
                        desc="C2-shaped 3D 7-point diffusion on 4x4x2 regions (profiling size)"),
+    "c5_elasticity": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3, power_iters=30,
+                          desc="3D linear elasticity, Q1 hexahedra, 3 dofs per node (81-coefficient "
+                               "block rows), 3x3x3 regions of 28^3 nodes (the paper's 82^3 "
+                               "elasticity mesh), E log-normal (sigma 0.5), nu 0.3, x=0 clamped, "
+                               "uniform body load; 30 power steps: 10 underestimate "
+                               "lambda_max(D^-1 A) by ~25% on this operator"),
+    "c5_elasticity_4x4x4": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                                power_iters=30,
+                                desc="3D linear elasticity as c5_elasticity on 4x4x4 regions of 28^3"),
+    "c3_q1laplace3d_slice": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                                 desc="3D Q1 Laplacian (27-point), 4x4x4 regions of 55^3 nodes "
+                                      "(the 4x4x4-region slice of the 8x8x8 configuration)"),
     "c4_highcontrast3d": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
                               desc="3D 7-point diffusion, 7x7x7 regions with per-axis node counts "
                                    "from {28,55,82} (seed 3), kappa constant per region, "
@@ -239,6 +259,12 @@ def main():
         p = W.diffusion3d_7pt(region_grid=(4, 4, 2), choices=(28, 55, 82), seed=1)
     elif args.workload == "c4_highcontrast3d":
         p = W.config("c4_highcontrast3d")
+    elif args.workload == "c5_elasticity":
+        p = W.elasticity3d(region_grid=(3, 3, 3), choices=(28,), seed=4)
+    elif args.workload == "c5_elasticity_4x4x4":
+        p = W.elasticity3d(region_grid=(4, 4, 4), choices=(28,), seed=4)
+    elif args.workload == "c3_q1laplace3d_slice":
+        p = W.q1_laplace3d(region_grid=(4, 4, 4), n=55, seed=2)
     else:
         p = W.config(args.workload)
     dp = upload(p, dev)
@@ -256,14 +282,21 @@ def main():
             o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, cfg["nu1"], cfg["nu2"], cfg["degree"]
         else:
             o.smoother, o.nu1, o.nu2, o.omega = rmg.JACOBI, cfg["nu1"], cfg["nu2"], cfg["omega"]
+        o.power_iters = cfg.get("power_iters", 10)
         return o
 
-    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    def set_operator():
+        if p.dofs_per_node > 1:
+            lay.operator_from_block_csr(p.stencil, p.dofs_per_node, dp.rowptr, dp.col, dp.val)
+        else:
+            lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+
+    set_operator()
     hier = rmg.Hierarchy(lay, options(args.precision))
-    x = torch.zeros(p.n_nodes, dtype=torch.float64, device=dev)
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev)
 
     def step(h):
-        lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+        set_operator()
         h.setup_numeric()
         x.zero_()
         return h.pcg(dp.b, x, rtol=RTOL, maxit=500, history=False)
@@ -303,7 +336,7 @@ def main():
     # per-phase breakdown of one step (outside the timed region)
     torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    e[0].record(stream); lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    e[0].record(stream); set_operator()
     e[1].record(stream); hier.setup_numeric()
     e[2].record(stream); x.zero_(); bi = hier.pcg(dp.b, x, rtol=RTOL, maxit=500, history=False)
     e[3].record(stream); torch.cuda.synchronize()
@@ -329,8 +362,9 @@ def main():
     kern_ms = probe_ms / max(1, probe_n)
     n_r0 = p.n_regional_nodes
     prec = args.precision
-    bytes_launch = SWEEP_BYTES[(prec, 7)] * n_r0 if p.stencil == 7 else None
-    flops_launch = SWEEP_FLOPS.get(p.stencil, 0) * n_r0
+    Bd = p.dofs_per_node
+    bytes_launch = sweep_bytes(prec, p.stencil, Bd) * n_r0
+    flops_launch = sweep_flops(p.stencil, Bd) * n_r0
     roofline = None
     if bytes_launch and kern_ms > 0:
         gbs = bytes_launch / (kern_ms / 1e3) / 1e9
@@ -348,7 +382,9 @@ def main():
             roofline = dict(bound="hbm", achieved=round(gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
                             frac=round(hbm_frac, 4), peak_src=pk["src"])
         tpn = profiled_traffic(prec)
-        roofline.update(kernel=f"k_stencil<{p.stencil}, EpiCheb> level 0 ({prec})",
+        tpn = tpn if (p.stencil == 7 and Bd == 1) else None
+        roofline.update(kernel=(f"k_stencil<{p.stencil}, EpiCheb> level 0 ({prec})" if Bd == 1 else
+                                f"k_bstencil<{p.stencil}, {Bd}, EpiCheb> level 0 ({prec})"),
                         traffic=(round(tpn * n_r0) if tpn else None),
                         traffic_src=("ncu dram__bytes per node (profiles/k_stencil7_cheb_c2quarter.md)"
                                      " x regional nodes" if tpn else None),
@@ -374,7 +410,9 @@ def main():
                    "unknowns": p.n_unknowns, "regional_nodes": p.n_regional_nodes,
                    "composite_nnz": int(p.A.nnz), "levels": cfg["levels"],
                    "precision": prec, "rtol": RTOL,
-                   "l2": "inputs larger than L2 (31.7M-node vectors, 1.8 GB stencils)",
+                   "dofs_per_node": p.dofs_per_node,
+                   "l2": "inputs larger than L2 (no flush needed)"
+                         if p.n_regional_nodes * 8 > 129e6 else "working set within L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "time_to_tol_s": ms_step / 1e3,
         "pcg_iterations": info["iterations"],
@@ -394,14 +432,15 @@ def main():
             msm, infm, _, (pms, pn) = timed(hm, args.steps, args.warmup)
             im = infm[-1]
             km = pms / max(1, pn)
-            bl = SWEEP_BYTES[(mp, 7)] * n_r0 if p.stencil == 7 else None
+            bl = sweep_bytes(mp, p.stencil, p.dofs_per_node) * n_r0
             mixed[mp] = dict(ms_per_step=msm / args.steps,
                              value=p.n_unknowns * im["vcycles"] * args.steps * world / (msm / 1e3),
                              pcg_iterations=im["iterations"], true_relres=im["true_relres"],
                              kernel_ms=km,
                              kernel_hbm_frac=(bl / (km / 1e3) / 1e9 / pk["hbm_gbs"]) if bl and km else None,
                              kernel_traffic=(round(profiled_traffic(mp) * n_r0)
-                                             if profiled_traffic(mp) else None),
+                                             if profiled_traffic(mp) and p.stencil == 7
+                                             and p.dofs_per_node == 1 else None),
                              speedup_vs_fp64=ms_step / (msm / args.steps))
             hm.close()
         out["mixed"] = mixed
@@ -409,7 +448,7 @@ def main():
     # learned prolongator: trained offline (outside the timed region) on small operators of the
     # same family labelled by the plain method; inside every timed step the network predicts
     # the level-0 weights from the new operator before the numeric setup
-    if not args.no_learned and p.stencil == 7:
+    if not args.no_learned and p.stencil == 7 and p.dofs_per_node == 1:
         from paper_2103_11962_gb300 import learned
         t0 = time.perf_counter()
         F, Y, M, factors = learned.training_set(ctx, range(args.train_operators),
@@ -421,7 +460,7 @@ def main():
         wr = torch.empty(3 * p.n_regional_nodes, dtype=torch.float32, device=dev)
 
         def lstep(h):
-            lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+            set_operator()
             h.mlp_weights(0, net, wr)
             h.set_transfer_weights(0, wr)
             h.setup_numeric()
@@ -456,7 +495,7 @@ def main():
     # CSR + right-hand side) from pinned memory, the step, D2H of the solution
     if not args.no_e2e:
         hp = {k: getattr(dp, k).cpu().pin_memory() for k in ("rowptr", "col", "val", "b")}
-        hx = torch.empty(p.n_nodes, dtype=torch.float64).pin_memory()
+        hx = torch.empty(p.n, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in hp.values())
         d2h = hx.numel() * hx.element_size()
 

@@ -70,7 +70,7 @@ typedef struct {
   int cheb_degree;       /* Chebyshev: updates of u per application (Algorithm 2)          */
   double eig_ratio;      /* Chebyshev interval [lambda/eig_ratio, boost*lambda] (Sec. 3.4) */
   double boost;
-  int power_iters;       /* power-method steps for lambda_max(D^-1 A)                      */
+  int power_iters;       /* power-method steps for lambda_max(D^-1 A), in [1, 100]        */
   int power_seed_base;   /* start vector of level l: SplitMix64 stream seed_base + l        */
   int precision;         /* rmg_precision                                                  */
   int use_graph;         /* capture the V-cycle in a CUDA graph (1) or launch eagerly (0)  */
@@ -203,6 +203,10 @@ rmg_status rmg_hier_set_transfer_weights(rmg_hier* hier, int level, const float*
  * 1/(-A_ij) of the three composite couplings on that line (the 1D A-harmonic extension,
  * linear for constant coefficients; linear where a coupling is not negative). */
 rmg_status rmg_hier_opdep_weights(rmg_hier* hier, int level, float* wr);
+/* Piecewise-constant 3:1 transfer weights of a level (the "Const" transfers of Table 4 and of
+ * the hybrid experiments, Sec. 6.4): every fine node takes weight 1 from its nearest coarse
+ * node along each axis; layout as above. Pass to rmg_hier_set_transfer_weights. */
+rmg_status rmg_hier_constant_weights(rmg_hier* hier, int level, float* wr);
 
 /*
  * Learned prolongator (no counterpart in the paper, which keeps linear interpolation and

@@ -76,3 +76,50 @@ def split_regional(layout: Layout, A: sp.csr_matrix) -> sp.csr_matrix:
 def split_composite_pieces(layout: Layout, A: sp.csr_matrix):
     """The n x n split matrices A^(k) = Psi_k (block k) Psi_k^T (for Lemma 1 checks)."""
     return [(Pk @ Bk @ Pk.T).tocsr() for Pk, Bk in zip(layout.Psi_k, split_blocks(layout, A))]
+
+
+def split_region_block(A: sp.csr_matrix, region_gids: np.ndarray, offsets: np.ndarray,
+                       k: int) -> sp.csr_matrix:
+    """Block Psi_k^T A^(k) Psi_k of a single region k, by the same rule as split_blocks
+    (A_ij / q_ij off the diagonal, z_i / mult_i minus the split off-diagonal row sum on it),
+    computed from region k and the regions that overlap it only. For operators too large for
+    the whole-problem form; split_blocks is its check on small problems."""
+    A = sp.csr_matrix(A)
+    gids = np.asarray(region_gids, dtype=np.int64)
+    n = A.shape[0]
+    gk = gids[offsets[k]:offsets[k + 1]]
+    mult = np.bincount(gids, minlength=n).astype(np.float64)
+    # regions that hold any node of region k: every region whose node set meets gk
+    inside = np.zeros(n, dtype=bool)
+    inside[gk] = True
+    region_of = np.repeat(np.arange(len(offsets) - 1), np.diff(offsets))
+    neighbours = np.unique(region_of[inside[gids]])
+    # membership of region k's nodes in each overlapping region, as bits of a mask
+    bits = np.zeros(gk.shape[0], dtype=np.int64)
+    for b, kk in enumerate(neighbours):
+        member = np.zeros(n, dtype=bool)
+        member[gids[offsets[kk]:offsets[kk + 1]]] = True
+        bits |= member[gk].astype(np.int64) << b
+    Bk = A[gk][:, gk].tocoo()
+    off = Bk.row != Bk.col
+    r, c, v = Bk.row[off], Bk.col[off], Bk.data[off]
+    q = _popcount(bits[r] & bits[c])          # regions holding both i and j
+    vs = v / q
+    offsum = np.bincount(r, weights=vs, minlength=gk.shape[0])
+    z = np.asarray(A[gk] @ np.ones(n)).ravel()
+    diag = z / mult[gk] - offsum
+    nk = gk.shape[0]
+    M = sp.csr_matrix((np.concatenate([vs, diag]),
+                       (np.concatenate([r, np.arange(nk)]), np.concatenate([c, np.arange(nk)]))),
+                      shape=(nk, nk))
+    return M
+
+
+def _popcount(x: np.ndarray) -> np.ndarray:
+    """Number of set bits of every entry (at most 63 overlapping regions)."""
+    x = np.asarray(x, dtype=np.int64)
+    count = np.zeros(x.shape, dtype=np.float64)
+    while np.any(x):
+        count += (x & 1)
+        x = x >> 1
+    return count

@@ -291,6 +291,14 @@ rmg_status rmg_hier_convergence_factor(rmg_hier* hh, int iters, unsigned long lo
   });
 }
 
+rmg_status rmg_hier_constant_weights(rmg_hier* hh, int level, float* wr) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(wr, RMG_ERR_ARG, "wr is NULL");
+    constant_weights(hh->h, level, wr);
+  });
+}
+
 rmg_status rmg_hier_lambda(rmg_hier* hh, int level, double* lam) {
   if (!hh || !lam) return RMG_ERR_ARG;
   Hier& h = hh->h;

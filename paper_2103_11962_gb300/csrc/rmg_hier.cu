@@ -411,8 +411,8 @@ void hier_build(Hier& h) {
               RMG_ERR_ARG, "unknown smoother");
   RMG_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, RMG_ERR_ARG, "cheb_degree in [1, 8]");
   RMG_REQUIRE(o.precision >= 0 && o.precision <= 2, RMG_ERR_ARG, "unknown precision");
-  RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1, RMG_ERR_ARG,
-              "bad Chebyshev options");
+  RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1 &&
+              o.power_iters <= 100, RMG_ERR_ARG, "bad Chebyshev options");
   h.lv.push_back(&h.layout->L0);
   for (int l = 1; l < o.levels; ++l) {
     h.own.emplace_back(new Level());
@@ -569,6 +569,14 @@ void set_transfer_weights(Hier& h, int level, const float* wr) {
   h.stored[level] = 1;
 }
 
+void constant_weights(Hier& h, int level, float* wr) {
+  RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
+  Level& L = *h.lv[level];
+  const Grid G = L.grid();
+  k_constant_weights<<<persistent_grid(*h.c, G.ntiles), kTile, 0, h.c->stream>>>(G, L.dim, wr);
+  RMG_LAUNCHED();
+}
+
 // Operator-dependent (series-resistance) weights of a level from its current operator.
 void opdep_weights(Hier& h, int level, float* wr) {
   RMG_REQUIRE(level >= 0 && level < h.levels(), RMG_ERR_ARG, "bad level");
@@ -592,8 +600,10 @@ void opdep_weights(Hier& h, int level, float* wr) {
 
 // lambda~_max(D~^-1 A) by the power method (Sec. 3.4). The start vector is normalised once;
 // the power_iters steps y <- D~^-1 A y then run without normalising (the direction is the
-// same as with a normalisation per step, and ||D~^-1 A|| <= 2 bounds the growth), and the
-// estimate is the Rayleigh quotient y^T D~^-1 A y / y^T y of the last iterate.
+// same as with a normalisation per step; the norm grows like lambda_max^k, and Gershgorin
+// bounds lambda_max(D~^-1 A) by 1 + sum_j |a_ij| / a_ii, a few units for the stencils here,
+// so 100 steps stay far inside the FP64 range), and the estimate is the Rayleigh quotient
+// y^T D~^-1 A y / y^T y of the last iterate.
 static void power_method(Hier& h, int l) {
   Ctx& c = *h.c;
   Level& L = *h.lv[l];

@@ -67,6 +67,7 @@ void vcycle(Hier& h);              // lv[0] rhs in v64[0].b (or v32[0].b) -> res
 void vcycle_apply(Hier& h, const double* r, double* z, int regional);
 void set_transfer_weights(Hier& h, int level, const float* wr);
 void opdep_weights(Hier& h, int level, float* wr);
+void constant_weights(Hier& h, int level, float* wr);
 double convergence_factor(Hier& h, int iters, unsigned long long seed);
 void pcg_solve(Hier& h, const double* b, double* x, double rtol, int maxit, double* history,
                rmg_solve_info* info);

@@ -315,6 +315,20 @@ k_opdep(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ mul
   RMG_END_FOR_NODES
 }
 
+// Piecewise-constant 3:1 transfers (the "Const" grid transfers of Table 4): every fine node
+// takes weight 1 from its nearest coarse node along each axis (remainder 1: the left one,
+// remainder 2: the right one), so each row of P has a single unit entry.
+__global__ void k_constant_weights(Grid G, int dim, float* __restrict__ wr) {
+  RMG_FOR_NODES(G)
+    int x[3];
+    decode(li, R, x[0], x[1], x[2]);
+    for (int a = 0; a < 3; ++a) {
+      const int rem = a < dim ? x[a] % 3 : 0;
+      wr[(size_t)a * G.n_r + n] = rem == 2 ? 1.f : 0.f;
+    }
+  RMG_END_FOR_NODES
+}
+
 // ------------------------------------------------------------------ power method (Sec. 3.4)
 // SplitMix64 as a counter-based generator: value i of stream seed = output i+1 of a
 // generator seeded with seed (Steele, Lea, Flood 2014). Doubles in [-1, 1) from the top 53 bits.

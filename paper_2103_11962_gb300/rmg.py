@@ -91,6 +91,7 @@ def lib():
         "rmg_launch_count": (ctypes.c_ulonglong, []),
         "rmg_hier_set_transfer_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
         "rmg_hier_opdep_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
+        "rmg_hier_constant_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
         "rmg_hier_convergence_factor": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_ulonglong,
                                                        ctypes.POINTER(ctypes.c_double)]),
         "rmg_mlp_num_params": (ctypes.c_int, []),
@@ -128,7 +129,7 @@ def exported_symbols():
             "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
             "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
-            "rmg_hier_opdep_weights", "rmg_hier_convergence_factor", "rmg_mlp_num_params", "rmg_mlp_create",
+            "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor", "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
             "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
 
@@ -323,6 +324,10 @@ class Hierarchy:
     def set_transfer_weights(self, level, wr):
         """Stored per-node interpolation weights for level -> level+1 (None = linear)."""
         self.ctx.check(lib().rmg_hier_set_transfer_weights(self.h, level, _ptr(wr)))
+
+    def constant_weights(self, level, wr):
+        """Piecewise-constant (nearest coarse node) weights of a level into wr (3 * n_r)."""
+        self.ctx.check(lib().rmg_hier_constant_weights(self.h, level, _ptr(wr)))
 
     def opdep_weights(self, level, wr):
         """Operator-dependent (series-resistance) weights of a level into wr (3 * n_r)."""

@@ -15,7 +15,8 @@ import workloads as W
 from oracle import cycle, hierarchy, krylov, smoothers
 from oracle.regions import make_layout
 from oracle.rng import splitmix64, uniform_pm1
-from oracle.split import split_blocks, split_composite_pieces, split_regional
+from oracle.split import (split_blocks, split_composite_pieces, split_region_block,
+                          split_regional)
 from oracle.transfer import composite_p, linear_p_1d
 
 pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
@@ -137,6 +138,19 @@ def test_split_entries_follow_rule(p3d):
                 # interior row w.r.t. Dirichlet: composite row sum is 0, so region row sum is 0
                 if abs(A.getrow(gi).sum()) < 1e-14:
                     assert abs(row.sum()) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["p2d", "p3d", "q3d"])
+def test_single_region_split_equals_whole_problem_split(name, request):
+    """The per-region split (used where the whole-problem form is too large) gives exactly the
+    blocks of the whole-problem split, which Lemma 1 pins."""
+    p = request.getfixturevalue(name)
+    lay = make_layout(p.region_dims, p.region_gids, p.n_nodes, p.dirichlet)
+    blocks = split_blocks(lay, p.A)
+    for k in range(lay.m):
+        Bk = split_region_block(p.A, p.region_gids, lay.offsets, k)
+        assert Bk.shape == blocks[k].shape
+        assert abs(Bk - blocks[k]).max() <= 1e-15 * abs(blocks[k]).max()
 
 
 def test_constant_coefficient_q1_split_equals_element_split():
@@ -645,3 +659,28 @@ def test_elasticity_regional_cycle_equals_composite(el3d):
     x, it, _ = krylov.pcg(levels[0].A, b, krylov.regional_preconditioner(rm), rtol=1e-12)
     xd = sp.linalg.spsolve(levels[0].A.tocsc(), b)
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_piecewise_constant_galerkin_closed_form():
+    """3:1 piecewise-constant transfers aggregate 3x3 fine nodes; the Galerkin product of the
+    5-point Laplacian is then 3 times the 5-point Laplacian on the coarse grid (three fine
+    edges cross every side of an aggregate; Table 4 'Const')."""
+    from oracle.transfer import stored_p
+    p = W.poisson2d_5pt(region_grid=(2, 2), n=28, seed=0)
+    Nx, Ny, _ = p.global_dims
+    g = np.arange(p.n_nodes)
+    coord = [g % Nx, g // Nx, np.zeros_like(g)]
+    wr = np.stack([(c % 3 == 2).astype(np.float32) for c in coord])
+    levels = hierarchy.build(p, 2, weights=lambda l, lev: wr)
+    P = levels[0].P
+    free = ~p.dirichlet.astype(bool)
+    rows = P[np.flatnonzero(free)]
+    assert np.all(np.diff(rows.indptr) <= 1)             # at most one coarse node per fine node
+    assert np.all(rows.data == 1.0)
+    c = levels[1]
+    cNx, cNy, _ = c.dims
+    x, y = cNx // 2, cNy // 2
+    row = c.A.getrow(x + cNx * y)
+    st = {(j % cNx - x, j // cNx - y): v for j, v in zip(row.indices, row.data) if v != 0}
+    assert st == pytest.approx({(0, 0): 12.0, (1, 0): -3.0, (-1, 0): -3.0, (0, 1): -3.0,
+                                (0, -1): -3.0})
