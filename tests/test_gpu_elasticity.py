@@ -12,6 +12,11 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
 
 
+# 10 power steps underestimate lambda_max(D^-1 A) of Q1 elasticity by more than the 1.1 boost,
+# so the elasticity hierarchies take 30 (as the elasticity bench workload does)
+POWER_ITERS = 30
+
+
 @pytest.fixture(scope="module")
 def ctx():
     from paper_2103_11962_gb300 import rmg
@@ -23,7 +28,8 @@ def case():
     from oracle import cycle, hierarchy
     p = W.elasticity3d(region_grid=(2, 2, 2), choices=(10, 19), seed=4)
     levels = hierarchy.build_block(p, 3)
-    mg = cycle.RegionalMG(levels, cycle.Options(smoother="chebyshev", nu1=1, nu2=1, degree=3))
+    mg = cycle.RegionalMG(levels, cycle.Options(smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                                                power_iters=POWER_ITERS))
     return p, levels, mg
 
 
@@ -33,7 +39,7 @@ def _gpu(ctx, p, precision=0):
     lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
     lay.operator_from_block_csr(27, 3, dp.rowptr, dp.col, dp.val)
     o = rmg.default_options(levels=3, smoother=rmg.CHEBYSHEV, nu1=1, nu2=1, cheb_degree=3,
-                            precision=precision)
+                            precision=precision, power_iters=POWER_ITERS)
     return dp, lay, rmg.Hierarchy(lay, o)
 
 
@@ -89,11 +95,8 @@ def test_block_apply_vcycle_and_pcg(ctx, case):
     print("elasticity PCG: gpu", res["iterations"], ["%.3e" % v for v in res["history"][-4:]],
           "oracle", it_or, ["%.3e" % v for v in hist_or[-4:]])
     assert res["converged"] and res["true_relres"] <= 1.5e-10
-    # elasticity is the worst-conditioned case: the two residual histories must agree closely,
-    # and the iteration counts may differ by one where the histories straddle 1e-10
-    k = min(len(hist_or), len(res["history"]))
-    assert rel_max(res["history"][:k], np.asarray(hist_or[:k])) <= 1e-3
-    assert abs(res["iterations"] - it_or) <= 1
+    assert res["iterations"] == it_or
+    assert np.abs(res["history"] / np.asarray(hist_or) - 1.0).max() <= 1e-6
     xo = np.empty(3 * n); xo[perm] = x_or
     assert np.linalg.norm(xg.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
 
