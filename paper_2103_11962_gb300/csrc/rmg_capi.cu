@@ -67,7 +67,7 @@ rmg_status rmg_create(rmg_ctx** out, int device, void* stream) {
     ctx->c.d_err.alloc(1);
     RMG_CUDA(cudaMemset(ctx->c.d_err.get(), 0, sizeof(int)));
     ctx->c.max_partials = ctx->c.nsm * 8;
-    ctx->c.partials.alloc(ctx->c.max_partials);
+    ctx->c.partials.alloc(2 * ctx->c.max_partials);   // room for two fused reductions
   });
   if (st != RMG_OK) {
     delete ctx;

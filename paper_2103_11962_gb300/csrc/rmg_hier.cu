@@ -80,6 +80,7 @@ __global__ void k_beta(Scalars* sc, int flexible) {
   sc->rz = sc->rz_new;
 }
 
+// x += alpha p, r -= alpha q, partial sums of r.r (all FP64).
 __global__ void __launch_bounds__(256)
 k_cg_update(int n, int n_nodes, const double* __restrict__ p, const double* __restrict__ q,
             const uint8_t* __restrict__ mult, const Scalars* __restrict__ sc,
@@ -90,10 +91,71 @@ k_cg_update(int n, int n_nodes, const double* __restrict__ p, const double* __re
     x[k] = x[k] + a * p[k];
     const double rk = r[k] - a * q[k];
     r[k] = rk;
-    s += (rk * rk) * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]);
+    s = fma(rk * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]), rk, s);
   }
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Mixed-precision cycle. GB300 retires two FP64 instructions per clock per SM (conversions
+// between FP32 and FP64 included), so the vector kernels around the FP32 cycle keep FP64 only
+// where the solution depends on it: x, r and p are FP64 and updated in FP64; the inner products
+// that only steer the flexible iteration (r.r for the stopping test, r.z and r.z_old for alpha
+// and beta) multiply the FP32 copy of r with the FP32 cycle output and add runs of 16 products
+// in FP32 into FP64 accumulators.
+constexpr int kRun = 16;
+
+// x += alpha p, r -= alpha q (FP64); r32 = FP32 copy of the new r (the cycle's right-hand
+// side); partial sums of r.r from r32.
+__global__ void __launch_bounds__(256)
+k_cg_update_mixed(int n, int n_nodes, const double* __restrict__ p, const double* __restrict__ q,
+                  const uint8_t* __restrict__ mult, const Scalars* __restrict__ sc,
+                  double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
+                  double* __restrict__ partials) {
+  const double a = sc->alpha;
+  double s = 0.0;
+  float run = 0.f;
+  int cnt = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    x[k] = fma(a, p[k], x[k]);
+    const double rk = fma(-a, q[k], r[k]);
+    r[k] = rk;
+    const float rf = (float)rk;
+    r32[k] = rf;
+    run = fmaf(rf * inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]), rf, run);
+    if (++cnt == kRun) { s += (double)run; run = 0.f; cnt = 0; }
+  }
+  s += (double)run;
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Partial sums of r.z and r.z_old from the FP32 residual copy and the FP32 cycle output, which
+// then becomes z_old. Partials of r.z go to partials[0, gridDim), those of r.z_old to
+// partials[gridDim, 2 gridDim).
+__global__ void __launch_bounds__(256)
+k_flex_dots(int n, int n_nodes, const float* __restrict__ r32, const float* __restrict__ z,
+            float* __restrict__ zold, const uint8_t* __restrict__ mult,
+            double* __restrict__ partials) {
+  double s0 = 0.0, s1 = 0.0;
+  float run0 = 0.f, run1 = 0.f;
+  int cnt = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const float rk = r32[k] * inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]);
+    const float zk = z[k];
+    run0 = fmaf(rk, zk, run0);
+    run1 = fmaf(rk, zold[k], run1);
+    zold[k] = zk;
+    if (++cnt == kRun) { s0 += (double)run0; s1 += (double)run1; run0 = run1 = 0.f; cnt = 0; }
+  }
+  s0 += (double)run0;
+  s1 += (double)run1;
+  s0 = block_sum<256>(s0);
+  s1 = block_sum<256>(s1);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s0;
+    partials[gridDim.x + blockIdx.x] = s1;
+  }
 }
 
 __global__ void k_axpy_neg(int n, const double* __restrict__ z, double* __restrict__ e) {
@@ -101,11 +163,12 @@ __global__ void k_axpy_neg(int n, const double* __restrict__ z, double* __restri
     e[k] -= z[k];
 }
 
-__global__ void k_p_update(int n, const double* __restrict__ z, const Scalars* __restrict__ sc,
+template <typename ZT>
+__global__ void k_p_update(int n, const ZT* __restrict__ z, const Scalars* __restrict__ sc,
                            double* __restrict__ p) {
   const double b = sc->beta;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    p[k] = z[k] + b * p[k];
+    p[k] = double(z[k]) + b * p[k];
 }
 
 // Composite inner product of consistent regional vectors with n entries (B components of
@@ -214,9 +277,7 @@ struct Exec {
         RMG_LAUNCHED();
         ++launches;
         if (C.ngroups) {
-          k_groups<VT><<<persistent_grid(c(), (C.ngroups + 255) / 256), 256, 0, st>>>(
-              C.ngroups, C.gptr.get(), C.gslot.get(), yb, EpiStore<VT>{wb});
-          RMG_LAUNCHED();
+          launch_groups(c(), C, (const VT*)yb, EpiStore<VT>{wb}, st);
           ++launches;
         }
       }
@@ -242,9 +303,7 @@ struct Exec {
     RMG_LAUNCHED();
     ++launches;
     if (C.ngroups) {
-      k_groups<VT><<<persistent_grid(c(), (C.ngroups + 255) / 256), 256, 0, st>>>(
-          C.ngroups, C.gptr.get(), C.gslot.get(), V(l + 1).y.get(), EpiStore<VT>{V(l + 1).b.get()});
-      RMG_LAUNCHED();
+      launch_groups(c(), C, (const VT*)V(l + 1).y.get(), EpiStore<VT>{V(l + 1).b.get()}, st);
       ++launches;
     }
   }
@@ -444,6 +503,7 @@ void hier_build(Hier& h) {
   const int n0 = h.lv[0]->B * h.lv[0]->n_r;
   h.x.alloc(n0); h.p.alloc(n0); h.q.alloc(n0); h.tmp.alloc(n0);
   h.r.alloc(n0); h.z.alloc(n0); h.zold.alloc(n0);
+  if (h.mixed()) h.zold32.alloc(n0);
   RMG_CUDA(cudaHostAlloc(&h.pinned, 64 * sizeof(double), cudaHostAllocDefault));
   RMG_CUDA(cudaEventCreate(&h.probe_ev[0]));
   RMG_CUDA(cudaEventCreate(&h.probe_ev[1]));
@@ -465,7 +525,8 @@ void hier_build(Hier& h) {
       h.cu2gid.get());
   RMG_LAUNCHED();
   const size_t nd = (size_t)std::max(1LL, ncd);
-  h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd);
+  h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd); h.Linv.alloc(nd * nd);
+  h.Dblk.alloc((size_t)((nd + kNB - 1) / kNB) * kNB * kNB);
   h.xc.alloc(nd); h.rc.alloc(nd);
   RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
@@ -489,9 +550,7 @@ static void compute_dinv(Hier& h, Level& L) {
     }
     RMG_LAUNCHED();
     if (L.ngroups) {
-      k_groups<double><<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
-          L.ngroups, L.gptr.get(), L.gslot.get(), yb, EpiRecip{db});
-      RMG_LAUNCHED();
+      launch_groups(c, L, (const double*)yb, EpiRecip{db}, c.stream);
     }
   }
 }
@@ -598,38 +657,65 @@ void opdep_weights(Hier& h, int level, float* wr) {
   RMG_LAUNCHED();
 }
 
-// lambda~_max(D~^-1 A) by the power method (Sec. 3.4). The start vector is normalised once;
-// the power_iters steps y <- D~^-1 A y then run without normalising (the direction is the
-// same as with a normalisation per step; the norm grows like lambda_max^k, and Gershgorin
-// bounds lambda_max(D~^-1 A) by 1 + sum_j |a_ij| / a_ii, a few units for the stencils here,
-// so 100 steps stay far inside the FP64 range), and the estimate is the Rayleigh quotient
+// Composite inner product of two consistent regional vectors of any precision (FP64 sums).
+template <typename VT>
+static void dot_t(Ctx& c, int n, int n_nodes, const VT* x, const VT* y, const uint8_t* mult,
+                  double* dst, int op, cudaStream_t st) {
+  const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
+  k_dot<VT, VT><<<g, 256, 0, st>>>(n, n_nodes, x, y, mult, c.partials.get());
+  RMG_LAUNCHED();
+  k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, dst, op);
+  RMG_LAUNCHED();
+}
+
+// lambda~_max(D~^-1 A) by the power method (Sec. 3.4), on the operator the cycle smooths with:
+// FP64 coefficients for the plain method, the FP32 or BF16 copies for the mixed cycle. The
+// start vector is normalised once; the power_iters steps y <- D~^-1 A y then run without
+// normalising (the direction is the same as with a normalisation per step; the norm grows like
+// lambda_max^k, and Gershgorin bounds lambda_max(D~^-1 A) by 1 + sum_j |a_ij| / a_ii, a few
+// units for the stencils here, so 100 steps stay far inside the FP64 range). In FP32 the
+// iterate is renormalised every 8 steps instead. The estimate is the Rayleigh quotient
 // y^T D~^-1 A y / y^T y of the last iterate.
-static void power_method(Hier& h, int l) {
+template <typename VT, typename CT>
+static void power_method_t(Hier& h, int l) {
   Ctx& c = *h.c;
   Level& L = *h.lv[l];
   cudaStream_t st = c.stream;
-  LevelVecs<double>& V = h.v64[l];
+  Exec<VT, CT> ex(h, st);
+  LevelVecs<VT>& V = ex.V(l);
+  const CT* coef = ex.coef(l);
+  const VT* dinv = ex.dinv(l);
   const int n = L.B * L.n_r, eg = persistent_grid(c, (n + 255) / 256);
   Scalars* sc = h.sc.get();
-  k_power_init<<<eg, 256, 0, st>>>(L.n_r, L.B, L.gid.get(), L.mask.get(),
-                                   (unsigned long long)(h.o.power_seed_base + l), V.u.get());
+  auto normalise = [&](VT* v) {
+    dot_t<VT>(c, n, L.n_r, v, v, L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
+    k_scale_div<VT><<<eg, 256, 0, st>>>(n, v, &sc->pw_norm, v);
+    RMG_LAUNCHED();
+  };
+  k_power_init<VT><<<eg, 256, 0, st>>>(L.n_r, L.B, L.gid.get(), L.mask.get(),
+                                       (unsigned long long)(h.o.power_seed_base + l), V.u.get());
   RMG_LAUNCHED();
-  dot(c, n, L.n_r, V.u.get(), V.u.get(), L.mult.get(), &sc->pw_norm, FIN_SQRT, st);
-  k_scale_div<<<eg, 256, 0, st>>>(n, V.u.get(), &sc->pw_norm, V.u.get());
-  RMG_LAUNCHED();
-  double* a = V.u.get();
-  double* b = V.r.get();
+  normalise(V.u.get());
+  VT* a = V.u.get();
+  VT* b = V.r.get();
   for (int it = 0; it < h.o.power_iters; ++it) {
-    launch_stencil(c, L, L.coef.get(), a, V.y.get(), EpiScaled<double>{L.dinv.get(), b}, st,
-                   nullptr);
+    launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr);
     std::swap(a, b);
+    if (sizeof(VT) < 8 && (it + 1) % 8 == 0 && it + 1 < h.o.power_iters) normalise(a);
   }
-  launch_stencil(c, L, L.coef.get(), a, V.y.get(), EpiScaled<double>{L.dinv.get(), b}, st,
-                 nullptr);
-  dot(c, n, L.n_r, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
-  dot(c, n, L.n_r, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
+  launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr);
+  dot_t<VT>(c, n, L.n_r, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
+  dot_t<VT>(c, n, L.n_r, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
   k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
   RMG_LAUNCHED();
+}
+
+static void power_method(Hier& h, int l) {
+  switch (h.o.precision) {
+    case RMG_PREC_FP64: power_method_t<double, double>(h, l); break;
+    case RMG_PREC_FP32: power_method_t<float, float>(h, l); break;
+    default: power_method_t<float, __nv_bfloat16>(h, l); break;
+  }
 }
 
 static void coarse_factor(Hier& h) {
@@ -657,12 +743,13 @@ static void coarse_factor(Hier& h) {
   RMG_CUDA(cudaMemcpyAsync(h.X.get(), h.Mfac.get(), (size_t)nc * nc * sizeof(double),
                            cudaMemcpyDeviceToDevice, st));
   for (int k0 = 0; k0 < nc; k0 += kNB) {
-    k_chol_diag<<<1, 256, 0, st>>>(h.Mfac.get(), nc, k0, c.d_err.get());
+    k_chol_diag<<<1, 32, 0, st>>>(h.Mfac.get(), nc, k0, h.Dblk.get(), c.d_err.get());
     RMG_LAUNCHED();
     const int k1 = std::min(nc, k0 + kNB);
     if (k1 < nc) {
       const int rows = nc - k1;
-      k_chol_panel<<<std::max(1, (rows + 127) / 128), 128, 0, st>>>(h.Mfac.get(), nc, k0);
+      k_chol_panel<<<std::min(1024, (rows + 7) / 8), 256, 0, st>>>(h.Mfac.get(), nc, k0,
+                                                                  h.Dblk.get());
       RMG_LAUNCHED();
       const int tiles = (rows + 15) / 16;
       k_chol_update<<<dim3(tiles, tiles), dim3(16, 16), 0, st>>>(h.Mfac.get(), nc, k0, k1);
@@ -670,14 +757,16 @@ static void coarse_factor(Hier& h) {
     }
   }
   c.check_device_error("rmg_setup (coarse factorisation)");
-  // the assembled matrix is kept in Ainv's slot until the inverse overwrites it
-  DBuf<double> Linv((size_t)nc * nc);
-  k_trinv<<<std::max(1, (nc + 7) / 8), 256, 0, st>>>(h.Mfac.get(), nc, Linv.get());
-  RMG_LAUNCHED();
+  // X = L^-1 block row by block row, then Ainv = X^T X
+  RMG_CUDA(cudaMemsetAsync(h.Linv.get(), 0, (size_t)nc * nc * sizeof(double), st));
+  const int nblk = (nc + kNB - 1) / kNB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    k_trinv_row<<<bi + 1, 256, 0, st>>>(h.Mfac.get(), nc, bi, h.Dblk.get(), h.Linv.get());
+    RMG_LAUNCHED();
+  }
   const int t = (nc + 15) / 16;
-  k_xtx<<<dim3(t, t), dim3(16, 16), 0, st>>>(Linv.get(), nc, h.Ainv.get());
+  k_xtx<<<dim3(t, t), dim3(16, 16), 0, st>>>(h.Linv.get(), nc, h.Ainv.get());
   RMG_LAUNCHED();
-  RMG_CUDA(cudaStreamSynchronize(st));
 }
 
 static void make_low_precision(Hier& h) {
@@ -713,10 +802,11 @@ void hier_numeric(Hier& h) {
     galerkin(h, l, *h.lv[l], *h.lv[l + 1]);
     compute_dinv(h, *h.lv[l + 1]);
   }
+  // the mixed cycle's coefficient copies first: its power method runs on them
+  if (h.mixed()) make_low_precision(h);
   if (h.o.smoother == RMG_SMOOTHER_CHEBYSHEV)
     for (int l = 0; l + 1 < Lv; ++l) power_method(h, l);
   coarse_factor(h);
-  if (h.mixed()) make_low_precision(h);
   RMG_CUDA(cudaMemcpyAsync(&h.hsc, h.sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
   const std::vector<char>& stored = h.stored;
@@ -871,26 +961,33 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   double relres = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
   if (history) history[0] = relres;
   int it = 0, ncyc = 0;
-  auto precondition = [&]() {
-    if (mixed) {
-      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, rvec, h.v32[0].b.get());
-      RMG_LAUNCHED();
-      vcycle(h);
-      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, h.v32[0].u.get(), zvec);
-      RMG_LAUNCHED();
-    } else {
-      vcycle(h);
-    }
-    ++ncyc;
-  };
+  // The FP32 cycle reads its right-hand side from r32 and leaves z32; in the loop, r32 is
+  // written by the CG update and z32 is read directly by the dots and the direction update
+  // (the cycle does not modify its level-0 right-hand side, so r32 stays valid for the dots).
+  float* r32 = mixed ? h.v32[0].b.get() : nullptr;
+  const float* z32 = mixed ? h.v32[0].u.get() : nullptr;
   int status_conv = 0;
   if (relres > rtol && bnorm > 0) {
-    precondition();
-    dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
-    k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.p.get());
-    RMG_LAUNCHED();
     if (mixed) {
-      k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, rvec, r32);
+      RMG_LAUNCHED();
+    }
+    vcycle(h);
+    ++ncyc;
+    if (mixed) {
+      const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
+      k_dot<double, float><<<g, 256, 0, st>>>(n, L0.n_r, rvec, z32, L0.mult.get(),
+                                               c.partials.get());
+      RMG_LAUNCHED();
+      k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, &sc->rz, FIN_STORE);
+      RMG_LAUNCHED();
+      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, z32, h.p.get());
+      RMG_LAUNCHED();
+      k_copy<float><<<eg, 256, 0, st>>>(n, z32, h.zold32.get());
+      RMG_LAUNCHED();
+    } else {
+      dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
+      k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.p.get());
       RMG_LAUNCHED();
     }
     for (it = 1; it <= maxit; ++it) {
@@ -899,8 +996,12 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       dot(c, n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), &sc->pq, FIN_STORE, st);
       k_alpha<<<1, 1, 0, st>>>(sc);
       RMG_LAUNCHED();
-      k_cg_update<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc, h.x.get(),
-                                     rvec, c.partials.get());
+      if (mixed)
+        k_cg_update_mixed<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc,
+                                              h.x.get(), rvec, r32, c.partials.get());
+      else
+        k_cg_update<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc,
+                                        h.x.get(), rvec, c.partials.get());
       RMG_LAUNCHED();
       k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rr, FIN_STORE);
       RMG_LAUNCHED();
@@ -908,17 +1009,27 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       relres = std::sqrt(rr) / bnorm;
       if (history) history[it] = relres;
       if (relres <= rtol) { status_conv = 1; break; }
-      precondition();
-      dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
+      vcycle(h);
+      ++ncyc;
       if (mixed) {
-        dot(c, n, L0.n_r, rvec, h.zold.get(), L0.mult.get(), &sc->beta, FIN_STORE, st);
-        k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+        k_flex_dots<<<dg, 256, 0, st>>>(n, L0.n_r, r32, z32, h.zold32.get(), L0.mult.get(),
+                                        c.partials.get());
+        RMG_LAUNCHED();
+        k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rz_new, FIN_STORE);
+        RMG_LAUNCHED();
+        k_finalize<<<1, 256, 0, st>>>(c.partials.get() + dg, dg, &sc->beta, FIN_STORE);
+        RMG_LAUNCHED();
+        k_beta<<<1, 1, 0, st>>>(sc, 1);
+        RMG_LAUNCHED();
+        k_p_update<float><<<eg, 256, 0, st>>>(n, z32, sc, h.p.get());
+        RMG_LAUNCHED();
+      } else {
+        dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
+        k_beta<<<1, 1, 0, st>>>(sc, 0);
+        RMG_LAUNCHED();
+        k_p_update<double><<<eg, 256, 0, st>>>(n, zvec, sc, h.p.get());
         RMG_LAUNCHED();
       }
-      k_beta<<<1, 1, 0, st>>>(sc, mixed ? 1 : 0);
-      RMG_LAUNCHED();
-      k_p_update<<<eg, 256, 0, st>>>(n, zvec, sc, h.p.get());
-      RMG_LAUNCHED();
     }
     if (it > maxit) it = maxit;
   } else {

@@ -31,6 +31,7 @@ struct Hier {
   DBuf<int> cidx, cu2slot;
   DBuf<long long> cu2gid;
   DBuf<double> Mfac, X, Ainv, xc, rc;
+  DBuf<double> Linv, Dblk;                   // L^-1 and the inverted 32 x 32 diagonal blocks
   // graph of one V-cycle
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -53,6 +54,7 @@ struct Hier {
   DBuf<float> mlp_feats, mlp_out;
   // PCG work vectors (regional, FP64)
   DBuf<double> x, r, z, p, q, zold, tmp;
+  DBuf<float> zold32;                        // previous FP32 cycle output (flexible CG)
   double* pinned = nullptr;                  // host-mapped residual read-back
 
   ~Hier();

@@ -131,7 +131,16 @@ inline int coarse_kind(int kind) { return (kind == 5 || kind == 9) ? 9 : 27; }
 struct RegionDev {
   int nx, ny, nz, pad;
   int off;     // first regional node of the region
+  float rnx, rny;   // 1/nx, 1/ny for the division-free index decode (0: exact integer path)
 };
+
+// Region descriptor with the reciprocals of decode(): regions of fewer than 2^22 nodes take the
+// float path (exact after one correction step), larger ones the integer division.
+__host__ __device__ inline RegionDev make_region(int nx, int ny, int nz, int off) {
+  const bool fast = (long long)nx * ny * nz < (1LL << 22);
+  return RegionDev{nx, ny, nz, 0, off, fast ? 1.0f / (float)nx : 0.0f,
+                   fast ? 1.0f / (float)ny : 0.0f};
+}
 
 struct Tile {   // a run of up to kTile consecutive nodes of one region
   int region;
@@ -173,6 +182,8 @@ struct Level {
   int ngroups = 0, nslots = 0;
   DBuf<int> gptr;                // ngroups + 1
   DBuf<int> gslot;               // regional slots of every group, ascending
+  DBuf<int> rid;                 // region of every regional node (built for the split)
+  DBuf<int> sgrp;                // group of every group slot (nslots)
   // operator
   DBuf<double> coef;             // kind * n_r, slot-major
   DBuf<double> dinv;             // 1 / (Psi^T Psi diag([[A]]))

@@ -16,11 +16,28 @@
 
 namespace rmg {
 
+// a / d for 0 <= a < 2^22 from the float reciprocal rd of d: the truncated product is within
+// one of the quotient (relative error below 2^-22 on a value below 2^22), and one correction
+// step makes it exact.
+__device__ __forceinline__ int div_rcp(int a, int d, float rd) {
+  int q = __float2int_rz(__int2float_rn(a) * rd);
+  const int r = a - q * d;
+  q += (r >= d) - (r < 0);
+  return q;
+}
+
 __device__ __forceinline__ void decode(int li, const RegionDev& R, int& i, int& j, int& l) {
-  i = li % R.nx;
-  const int rest = li / R.nx;
-  j = rest % R.ny;
-  l = rest / R.ny;
+  if (R.rnx != 0.0f) {
+    const int rest = div_rcp(li, R.nx, R.rnx);
+    i = li - rest * R.nx;
+    l = div_rcp(rest, R.ny, R.rny);
+    j = rest - l * R.ny;
+  } else {
+    i = li % R.nx;
+    const int rest = li / R.nx;
+    j = rest % R.ny;
+    l = rest / R.ny;
+  }
 }
 
 __device__ __forceinline__ void set_err(int* err, int code) {
@@ -90,16 +107,19 @@ k_stencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
   RMG_END_FOR_NODES
 }
 
-// Phase B: interface groups. y holds the partial row results of every copy.
+// Phase B: interface groups. y holds the partial row results of every copy. One thread per
+// copy: it sums the partial results of its group in ascending slot order (every copy of a group
+// forms the identical sum) and applies the epilogue to its own copy.
 template <typename AT, class Epi>
 __global__ void __launch_bounds__(256)
-k_groups(int ngroups, const int* __restrict__ gptr, const int* __restrict__ gslot,
-         const AT* __restrict__ y, Epi epi) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+k_groups(int nslots, const int* __restrict__ sgrp, const int* __restrict__ gptr,
+         const int* __restrict__ gslot, const AT* __restrict__ y, Epi epi) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += gridDim.x * blockDim.x) {
+    const int g = sgrp[q];
     const int a = gptr[g], e = gptr[g + 1];
     AT s = AT(0);
     for (int k = a; k < e; ++k) s += y[gslot[k]];
-    for (int k = a; k < e; ++k) epi(gslot[k], s, e - a);
+    epi(gslot[q], s, e - a);
   }
 }
 
@@ -335,21 +355,21 @@ k_restrict(Grid Gc, const RegionDev* __restrict__ fregions, const VT* __restrict
   RMG_END_FOR_NODES
 }
 
-// Region-local interpolation and correction u += [[P]] ubar (no inter-region exchange).
-// The products wz (wy wx) of the up to 8 weights of a fine node come from a shared table
-// indexed by the three remainders.
+// Weight of the right coarse neighbour of a fine node with remainder rem (the left one takes
+// 1 - w): 0, 1/3, 2/3, compile-time constants in the vector precision.
+template <typename VT>
+__device__ __forceinline__ VT rem_weight(int rem) {
+  return rem == 0 ? VT(0) : (rem == 1 ? VT(1.0 / 3.0) : VT(2.0 / 3.0));
+}
+
+// Region-local interpolation and correction u += [[P]] ubar (no inter-region exchange). Every
+// fine node gathers the 2 x 2 (x 2) coarse nodes around it and combines them axis by axis with
+// the weights (1 - w, w) of its remainders; a right neighbour past the region edge only occurs
+// with remainder 0 (weight 0) and is clamped onto the left one.
 template <int DIM, typename VT>
 __global__ void __launch_bounds__(kTile)
 k_prolong(Grid Gf, const RegionDev* __restrict__ cregions, const uint8_t* __restrict__ fmask,
           const VT* __restrict__ ubar, VT* __restrict__ u) {
-  __shared__ VT tab[27 * 8];
-  for (int e = threadIdx.x; e < 27 * 8; e += blockDim.x) {
-    const int r = e >> 3, combo = e & 7;
-    const int rx = r % 3, ry = (r / 3) % 3, rz = r / 9;
-    const int sa = combo & 1, sb = (combo >> 1) & 1, sc = combo >> 2;
-    tab[e] = VT(wrem(rz, sc) * (wrem(ry, sb) * wrem(rx, sa)));
-  }
-  __syncthreads();
   RMG_FOR_NODES(Gf)
     if (fmask[n]) continue;
     int i, j, l;
@@ -358,14 +378,21 @@ k_prolong(Grid Gf, const RegionDev* __restrict__ cregions, const uint8_t* __rest
     const int cx = i / 3, rx = i - 3 * cx;
     const int cy = j / 3, ry = j - 3 * cy;
     const int cz = DIM == 3 ? l / 3 : 0, rz = DIM == 3 ? l - 3 * cz : 0;
-    const int nxs = rx ? 2 : 1, nys = ry ? 2 : 1, nzs = rz ? 2 : 1;
-    const VT* t = tab + 8 * (rx + 3 * ry + 9 * rz);
-    const int base = C.off + cx + C.nx * (cy + C.ny * cz);
-    VT acc = VT(0);
-    for (int c = 0; c < nzs; ++c)
-      for (int b = 0; b < nys; ++b)
-        for (int a = 0; a < nxs; ++a)
-          acc = fma(t[a + 2 * b + 4 * c], ubar[base + a + C.nx * (b + C.ny * c)], acc);
+    const int sy = C.nx, sz = C.nx * C.ny;
+    const int dx = cx + 1 < C.nx ? 1 : 0;
+    const int dy = cy + 1 < C.ny ? sy : 0;
+    const int dz = (DIM == 3 && cz + 1 < C.nz) ? sz : 0;
+    const VT* b0 = ubar + C.off + cx + sy * cy + sz * cz;
+    const VT wx1 = rem_weight<VT>(rx), wx0 = VT(1) - wx1;
+    const VT wy1 = rem_weight<VT>(ry), wy0 = VT(1) - wy1;
+    auto xline = [&](const VT* p) { return fma(wx1, p[dx], wx0 * p[0]); };
+    const VT a0 = fma(wy1, xline(b0 + dy), wy0 * xline(b0));
+    VT acc = a0;
+    if (DIM == 3) {
+      const VT wz1 = rem_weight<VT>(rz), wz0 = VT(1) - wz1;
+      const VT a1 = fma(wy1, xline(b0 + dz + dy), wy0 * xline(b0 + dz));
+      acc = fma(wz1, a1, wz0 * a0);
+    }
     u[n] = u[n] + acc;
   RMG_END_FOR_NODES
 }
@@ -477,7 +504,9 @@ k_dot(int n, int n_nodes, const XT* __restrict__ x, const YT* __restrict__ y,
       const uint8_t* __restrict__ mult, double* __restrict__ partials) {
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    s += (double(x[k]) * double(y[k])) * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]);
+    // with the multiplicities of box tilings (1, 2, 4, 8) x * (1/mult) is exact and the FMA
+    // rounds once
+    s = fma(double(x[k]) * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]), double(y[k]), s);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }

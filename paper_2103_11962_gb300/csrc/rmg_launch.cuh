@@ -6,6 +6,15 @@
 
 namespace rmg {
 
+// Phase B alone (scalar levels): one thread per copy of every interface group.
+template <typename AT, class Epi>
+void launch_groups(Ctx& c, const Level& L, const AT* y, Epi epi, cudaStream_t st) {
+  if (!L.ngroups) return;
+  const int gs = persistent_grid(c, (L.nslots + 255) / 256);
+  k_groups<AT><<<gs, 256, 0, st>>>(L.nslots, L.sgrp.get(), L.gptr.get(), L.gslot.get(), y, epi);
+  RMG_LAUNCHED();
+}
+
 template <class Epi, typename CT, typename VT, typename AT>
 void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
                     cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
@@ -33,12 +42,13 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
   if (ev1) RMG_CUDA(cudaEventRecordWithFlags(ev1, st, g_capturing ? cudaEventRecordExternal : 0));
   if (launches) ++*launches;
   if (L.ngroups) {
-    const int gg = persistent_grid(c, (L.ngroups + 255) / 256);
-    if (L.B == 1)
-      k_groups<AT><<<gg, 256, 0, st>>>(L.ngroups, L.gptr.get(), L.gslot.get(), y, epi);
-    else
+    if (L.B == 1) {
+      launch_groups(c, L, y, epi, st);
+    } else {
+      const int gg = persistent_grid(c, (L.ngroups + 255) / 256);
       k_groups_b<AT><<<gg, 256, 0, st>>>(L.ngroups, L.B, L.n_r, L.gptr.get(), L.gslot.get(), y, epi);
-    RMG_LAUNCHED();
+      RMG_LAUNCHED();
+    }
     if (launches) ++*launches;
   }
 }

@@ -167,6 +167,12 @@ __global__ void k_group_fill(int n_r, const int* __restrict__ gid, const int* __
   }
 }
 
+// Group of every group slot (the inverse of gptr), for the slot-parallel phase B.
+__global__ void k_slot_groups(int ngroups, const int* __restrict__ gptr, int* __restrict__ sgrp) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x)
+    for (int q = gptr[g]; q < gptr[g + 1]; ++q) sgrp[q] = g;
+}
+
 __global__ void k_group_sort(int ngroups, const int* __restrict__ gptr, int* __restrict__ gslot) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
     const int a = gptr[g], e = gptr[g + 1];
@@ -195,7 +201,7 @@ void build_tiles(Level& L) {
                       cudaMemcpyHostToDevice));
   std::vector<RegionDev> hr(L.nreg);
   for (int r = 0; r < L.nreg; ++r)
-    hr[r] = RegionDev{L.hdims[3 * r], L.hdims[3 * r + 1], L.hdims[3 * r + 2], 0, L.hoff[r]};
+    hr[r] = make_region(L.hdims[3 * r], L.hdims[3 * r + 1], L.hdims[3 * r + 2], L.hoff[r]);
   L.regions.alloc(L.nreg);
   RMG_CUDA(cudaMemcpy(L.regions.get(), hr.data(), hr.size() * sizeof(RegionDev),
                       cudaMemcpyHostToDevice));
@@ -257,6 +263,12 @@ void build_groups(Ctx& c, Level& L, const uint8_t* dir_comp, const uint8_t* rmas
         L.ngroups, L.gptr.get(), L.gslot.get());
     RMG_LAUNCHED();
   }
+  L.sgrp.alloc(std::max(1, L.nslots));
+  if (L.ngroups) {
+    k_slot_groups<<<persistent_grid(c, (L.ngroups + 255) / 256), 256, 0, c.stream>>>(
+        L.ngroups, L.gptr.get(), L.sgrp.get());
+    RMG_LAUNCHED();
+  }
   RMG_CUDA(cudaStreamSynchronize(c.stream));
 }
 
@@ -302,29 +314,61 @@ __device__ __forceinline__ int copy_in_region(int cg, const RegionDev& R, int no
   return -1;
 }
 
-// Number of regions holding both composite nodes a and b (both shared, or one not).
-__device__ __forceinline__ int share_count(int a, int b, const RegionDev* __restrict__ regs,
-                                           int nreg, const int* __restrict__ cgrp,
+// Number of regions holding both composite nodes a and b. Group slots are ascending and
+// regions occupy ascending slot ranges, so the region ids of a group are ascending too and the
+// regions common to the two groups are found by one merge of the two lists.
+__device__ __forceinline__ int share_count(int a, int b, const int* __restrict__ rid,
+                                           const int* __restrict__ cgrp,
                                            const int* __restrict__ gptr,
                                            const int* __restrict__ gslot) {
   const int ga = cgrp[a], gb = cgrp[b];
   if (ga < 0 || gb < 0) return 1;
+  int p = gptr[ga], s = gptr[gb];
+  const int pe = gptr[ga + 1], se = gptr[gb + 1];
   int q = 0;
-  for (int p = gptr[ga]; p < gptr[ga + 1]; ++p) {
-    const int ra = region_of(regs, nreg, gslot[p]);
-    for (int s = gptr[gb]; s < gptr[gb + 1]; ++s)
-      if (region_of(regs, nreg, gslot[s]) == ra) { ++q; break; }
+  int ra = rid[gslot[p]], rb = rid[gslot[s]];
+  for (;;) {
+    if (ra == rb) {
+      ++q;
+      if (++p == pe || ++s == se) break;
+      ra = rid[gslot[p]];
+      rb = rid[gslot[s]];
+    } else if (ra < rb) {
+      if (++p == pe) break;
+      ra = rid[gslot[p]];
+    } else {
+      if (++s == se) break;
+      rb = rid[gslot[s]];
+    }
   }
   return q;
 }
 
-template <int KIND>
+__global__ void k_region_ids(Grid G, int* __restrict__ rid) {
+  RMG_FOR_NODES(G)
+    rid[n] = tile_.region;
+  RMG_END_FOR_NODES
+}
+
+// Offset (dx, dy, dz) of regional node n + d from node n of a region with row stride sy and
+// plane stride sz, for a neighbour inside the 3x3x3 box: peel the plane and row offsets off d
+// by comparison (exact when sy >= 3, since |dx| <= 1 < sy / 2 and |dx + sy dy| < sz / 2).
+__device__ __forceinline__ void box_offset(int d, int sy, int sz, int& dx, int& dy, int& dz) {
+  dz = 0;
+  if (2 * d > sz) { dz = 1; d -= sz; } else if (2 * d < -sz) { dz = -1; d += sz; }
+  dy = 0;
+  if (2 * d > sy) { dy = 1; d -= sy; } else if (2 * d < -sy) { dy = -1; d += sy; }
+  dx = d;
+}
+
+template <int KIND, int B>
 __global__ void __launch_bounds__(kTile)
 k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
             const int* __restrict__ c2r, const int* __restrict__ cgrp,
             const int* __restrict__ gptr, const int* __restrict__ gslot,
-            const int64_t* __restrict__ rowptr, const int64_t* __restrict__ col,
-            const double* __restrict__ val, int ncomp, int B, double* __restrict__ coef, int* err) {
+            const int* __restrict__ rid, const int64_t* __restrict__ rowptr,
+            const int64_t* __restrict__ col, const double* __restrict__ val, int ncomp,
+            double* __restrict__ coef, int* err) {
   using S = Sten<KIND>;
   // block (c, cp) of a B-dof operator: rows g*B + c, columns g'*B + cp (blockIdx.y = c*B + cp)
   const int c_row = blockIdx.y / B, c_col = blockIdx.y % B;
@@ -332,32 +376,57 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
     int i, j, l;
     decode(li, R, i, j, l);
     const int nodes = R.nx * R.ny * R.nz;
+    const int sy = R.nx, sz = R.nx * R.ny;
+    const bool peel = R.nx >= 3 && R.ny >= 3;    // box_offset is exact
     const int g = gid[n];
+    const bool shared = mult[n] > 1;
     double acc[S::S];
 #pragma unroll
     for (int s = 0; s < S::S; ++s) acc[s] = 0.0;
     double zsum = 0.0, offsum = 0.0;
+    unsigned seen = 0;                           // slots already filled (27 < 32 bits)
     const int64_t row = (int64_t)g * B + c_row;
-    for (int64_t e = rowptr[row]; e < rowptr[row + 1]; ++e) {
+    const int64_t e1 = rowptr[row + 1];
+    for (int64_t e = rowptr[row]; e < e1; ++e) {
       const int64_t c64 = col[e];
       const double v = val[e];
       if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); continue; }
-      if (c64 % B != c_col) continue;
-      const int c = (int)(c64 / B);
+      int c = (int)c64;
+      if (B > 1) {                                 // compile-time divisor: multiply-shift
+        c = (int)(c64 / B);
+        if ((int)(c64 - (int64_t)c * B) != c_col) continue;
+      }
       zsum += v;
       if (c == g) continue;
       const int sc = copy_in_region(c, R, nodes, c2r, cgrp, gptr, gslot);
       if (sc < 0) continue;                      // entry belongs to other regions only
-      int ic, jc, lc;
-      decode(sc - R.off, R, ic, jc, lc);
-      const int slot = sten_slot<KIND>(ic - i, jc - j, lc - l);
+      int dx, dy, dz;
+      if (peel) {
+        box_offset(sc - n, sy, sz, dx, dy, dz);
+      } else {
+        int ic, jc, lc;
+        decode(sc - R.off, R, ic, jc, lc);
+        dx = ic - i; dy = jc - j; dz = lc - l;
+      }
+      const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
+                          j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
+      const int slot = inside ? sten_slot<KIND>(dx, dy, dz) : -1;
       if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
-      const int q = share_count(g, c, G.regions, G.nreg, cgrp, gptr, gslot);
-      const double vs = v * inv_mult<double>(q);
+      const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
+      const double vs = q == 1 ? v : v * inv_mult<double>(q);
       offsum += vs;
+      // a CSR row holds one entry per neighbour: place it by selects (integer pipe) and keep
+      // the FP64 accumulation for the rare row with a repeated column
+      const unsigned bit = 1u << slot;
+      if (seen & bit) {
 #pragma unroll
-      for (int s = 0; s < S::S; ++s)
-        if (s == slot) acc[s] += vs;
+        for (int s = 0; s < S::S; ++s)
+          if (s == slot) acc[s] += vs;
+      } else {
+        seen |= bit;
+#pragma unroll
+        for (int s = 0; s < S::S; ++s) acc[s] = s == slot ? vs : acc[s];
+      }
     }
     acc[S::CENTER] = zsum * inv_mult<double>(mult[n]) - offsum;
     double* cb = coef + (size_t)blockIdx.y * S::S * G.n_r;
@@ -405,17 +474,22 @@ void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, co
   L.B = B;
   L.coef.ensure((size_t)B * B * kind * L.n_r);
   const Grid G = L.grid();
+  if (!L.rid.get()) {
+    L.rid.alloc(L.n_r);
+    k_region_ids<<<persistent_grid(c, G.ntiles), kTile, 0, c.stream>>>(G, L.rid.get());
+    RMG_LAUNCHED();
+  }
   const dim3 gb(persistent_grid(c, G.ntiles), B * B);
-#define RMG_SPLIT(K)                                                                        \
-  k_split_csr<K><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(),     \
-                                             L.cgrp.get(), L.gptr.get(), L.gslot.get(),      \
-                                             rowptr, col, val, L.ncomp, B, L.coef.get(), \
-                                             c.d_err.get())
+#define RMG_SPLIT(K, BB)                                                                    \
+  k_split_csr<K, BB><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(), \
+                                                 L.cgrp.get(), L.gptr.get(), L.gslot.get(),  \
+                                                 L.rid.get(), rowptr, col, val, L.ncomp,     \
+                                                 L.coef.get(), c.d_err.get())
   switch (kind) {
-    case 5: RMG_SPLIT(5); break;
-    case 7: RMG_SPLIT(7); break;
-    case 9: RMG_SPLIT(9); break;
-    default: RMG_SPLIT(27); break;
+    case 5: RMG_SPLIT(5, 1); break;
+    case 7: RMG_SPLIT(7, 1); break;
+    case 9: if (B == 3) RMG_SPLIT(9, 3); else RMG_SPLIT(9, 1); break;
+    default: if (B == 3) RMG_SPLIT(27, 3); else RMG_SPLIT(27, 1); break;
   }
 #undef RMG_SPLIT
   RMG_LAUNCHED();

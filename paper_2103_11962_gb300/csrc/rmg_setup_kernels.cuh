@@ -160,6 +160,10 @@ __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r
             for (int ox = -1; ox <= 1; ++ox) {
               const int ix = ox + bx, iy = oy + by, iz = oz + bz;
               if (ix < 0 || ix > 2 || iy < 0 || iy > 2 || iz < 0 || iz > 2) continue;
+              // (A P)(f, C + o) vanishes unless |f - 3 (C + o)| <= 3 on every axis (A reaches
+              // one node, P two): skip those structural zeros (compile-time, exact)
+              if (3 * ox - a > 3 || a - 3 * ox > 3 || 3 * oy - b > 3 || b - 3 * oy > 3) continue;
+              if (DIM == 3 && (3 * oz - c > 3 || c - 3 * oz > 3)) continue;
               const int slot = (ox + 1) + 3 * (oy + 1) + (DIM == 3 ? 9 * (oz + 1) : 0);
               acc[slot] = fma(wf, ap[(size_t)(ix + 3 * iy + 9 * iz) * fn_r + f], acc[slot]);
             }
@@ -342,13 +346,14 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
 
 // Random start vector: value of composite dof g*B + b (dofs numbered node-major) at every
 // copy of the node; zero at masked nodes. Regional vectors are component-major.
+template <typename VT>
 __global__ void k_power_init(int n_r, int B, const int* __restrict__ gid,
                              const uint8_t* __restrict__ mask, unsigned long long seed,
-                             double* __restrict__ x) {
+                             VT* __restrict__ x) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_r; k += gridDim.x * blockDim.x)
     for (int b = 0; b < B; ++b)
       x[(size_t)b * n_r + k] =
-          mask[k] ? 0.0 : splitmix_pm1(seed, (unsigned long long)gid[k] * B + b);
+          mask[k] ? VT(0) : VT(splitmix_pm1(seed, (unsigned long long)gid[k] * B + b));
 }
 
 // out = sum of partials, then an operation on the scalar block.
@@ -369,9 +374,10 @@ __global__ void k_finalize(const double* __restrict__ partials, int np, double* 
 }
 
 // out = x / ||x|| as a product with the stored reciprocal norm.
-__global__ void k_scale_div(int n, const double* __restrict__ x, const double* __restrict__ nrm,
-                            double* __restrict__ out) {
-  const double d = nrm[1];
+template <typename VT>
+__global__ void k_scale_div(int n, const VT* __restrict__ x, const double* __restrict__ nrm,
+                            VT* __restrict__ out) {
+  const VT d = VT(nrm[1]);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
     out[k] = x[k] * d;
 }
@@ -458,54 +464,79 @@ __global__ void k_coarse_assemble(int ncomp, int B, const RegionDev* __restrict_
   }
 }
 
-// Blocked right-looking Cholesky (lower), block width 32, in place in row-major M.
+// Blocked right-looking Cholesky (lower), block width 32, in place in row-major M, followed by
+// the explicit inverse Ainv = L^-T L^-1 for the coarse solve (one GEMV per cycle).
+//  k_chol_diag   one warp factors the 32 x 32 diagonal block and inverts it (Dinv_k = L_kk^-1);
+//  k_chol_panel  L_ik = A_ik L_kk^-T as a product with Dinv_k (no serial solve per row);
+//  k_chol_update trailing update of the lower triangle;
+//  k_trinv_row   block row i of X = L^-1: X_ij = -Dinv_i sum_{k=j}^{i-1} L_ik X_kj, X_ii = Dinv_i;
+//  k_xtx         Ainv = X^T X (lower tiles, mirrored).
+// A partial last block is padded with the identity inside the kernels.
 constexpr int kNB = 32;
 
-__global__ void k_chol_diag(double* M, int n, int k0, int* err) {
+__global__ void __launch_bounds__(32)
+k_chol_diag(double* M, int n, int k0, double* __restrict__ Dblk, int* err) {
   __shared__ double T[kNB][kNB + 1];
+  __shared__ double X[kNB][kNB + 1];
+  __shared__ double rdiag[kNB];
   const int nb = min(kNB, n - k0);
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    T[i][j] = (i < nb && j < nb) ? M[(size_t)(k0 + i) * n + k0 + j] : 0.0;
-  }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      const double p = T[j][j];
-      if (!(p > 0.0)) { set_err(err, DERR_NOT_SPD); T[j][j] = 1.0; }
-      else T[j][j] = sqrt(p);
+  const int ln = threadIdx.x;
+  for (int i = 0; i < kNB; ++i)
+    T[i][ln] = (i < nb && ln < nb) ? M[(size_t)(k0 + i) * n + k0 + ln] : (i == ln ? 1.0 : 0.0);
+  __syncwarp();
+  for (int j = 0; j < kNB; ++j) {
+    double p = T[j][j];
+    if (!(p > 0.0)) {
+      if (ln == 0) set_err(err, DERR_NOT_SPD);
+      p = 1.0;
     }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) T[i][j] /= T[j][j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      const int i = e / nb, c = e % nb;
-      if (i > j && c > j && c <= i) T[i][c] -= T[i][j] * T[c][j];
+    const double d = sqrt(p);
+    const double rd = 1.0 / d;
+    __syncwarp();
+    if (ln == j) { T[j][j] = d; rdiag[j] = rd; }
+    if (ln > j) T[ln][j] *= rd;
+    __syncwarp();
+    if (ln > j) {
+      const double lij = T[ln][j];
+      for (int c = j + 1; c <= ln; ++c) T[ln][c] -= lij * T[c][j];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e % nb;
-    M[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? T[i][j] : 0.0;
+  // column ln of L^-1 by forward substitution (each lane owns one column)
+  for (int i = 0; i < kNB; ++i) {
+    double x = 0.0;
+    if (i >= ln) {
+      double s = i == ln ? 1.0 : 0.0;
+      for (int m = ln; m < i; ++m) s -= T[i][m] * X[m][ln];
+      x = s * rdiag[i];
+    }
+    X[i][ln] = x;
+  }
+  __syncwarp();
+  double* D = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
+  for (int i = 0; i < kNB; ++i) {
+    D[i * kNB + ln] = X[i][ln];
+    if (i < nb && ln < nb) M[(size_t)(k0 + i) * n + k0 + ln] = ln <= i ? T[i][ln] : 0.0;
   }
 }
 
-__global__ void k_chol_panel(double* M, int n, int k0) {
-  __shared__ double Lk[kNB][kNB + 1];
+__global__ void __launch_bounds__(256)
+k_chol_panel(double* M, int n, int k0, const double* __restrict__ Dblk) {
+  __shared__ double D[kNB][kNB + 1], A[8][kNB + 1];
   const int nb = min(kNB, n - k0);
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    Lk[i][j] = (i < nb && j < nb) ? M[(size_t)(k0 + i) * n + k0 + j] : 0.0;
-  }
-  __syncthreads();
-  for (int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double x[kNB];
-    for (int j = 0; j < nb; ++j) {
-      double a = M[(size_t)i * n + k0 + j];
-      for (int k = 0; k < j; ++k) a -= x[k] * Lk[j][k];
-      x[j] = a / Lk[j][j];
+  const double* Dk = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) D[e / kNB][e % kNB] = Dk[e];
+  const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
+  for (int rb = k0 + nb + blockIdx.x * 8; rb < n; rb += gridDim.x * 8) {
+    __syncthreads();
+    const int r = rb + tr;
+    A[tr][tc] = (r < n && tc < nb) ? M[(size_t)r * n + k0 + tc] : 0.0;
+    __syncthreads();
+    if (r < n && tc < nb) {
+      double s = 0.0;
+      for (int m = 0; m <= tc; ++m) s = fma(A[tr][m], D[tc][m], s);
+      M[(size_t)r * n + k0 + tc] = s;
     }
-    for (int j = 0; j < nb; ++j) M[(size_t)i * n + k0 + j] = x[j];
   }
 }
 
@@ -531,42 +562,77 @@ __global__ void k_chol_update(double* M, int n, int k0, int k1) {
   }
 }
 
-// Xc = (L^-1)^T stored row by row: row j of Xc is column j of L^-1. One warp per column:
-// forward substitution, the dot product over earlier rows split across the lanes.
-__global__ void k_trinv(const double* __restrict__ L, int n, double* __restrict__ Xc) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int j = warp; j < n; j += nwarps) {
-    double* x = Xc + (size_t)j * n;
-    for (int i = lane; i < j; i += 32) x[i] = 0.0;
-    for (int i = j; i < n; ++i) {
-      const double* Li = L + (size_t)i * n;
-      double s = 0.0;
-      for (int k = j + lane; k < i; k += 32) s = fma(Li[k], x[k], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
-      __syncwarp();
+// Block row bi of X = L^-1 (row-major, lower; the upper part is zero beforehand). CTA j
+// computes X_{bi, j}; CTA bi copies Dinv_bi onto the diagonal. Thread (ty, tx) of the 32 x 8
+// layout owns rows ty, ty + 8, ty + 16, ty + 24 of column tx.
+__global__ void __launch_bounds__(256)
+k_trinv_row(const double* __restrict__ L, int n, int bi, const double* __restrict__ Dblk,
+            double* __restrict__ X) {
+  __shared__ double As[kNB][kNB + 1], Bs[kNB][kNB + 1];
+  const int bj = blockIdx.x;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = bi * kNB, j0 = bj * kNB;
+  const double* Di = Dblk + (size_t)bi * kNB * kNB;
+  if (bj == bi) {
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      if (i0 + r < n && j0 + tx < n) X[(size_t)(i0 + r) * n + j0 + tx] = Di[r * kNB + tx];
     }
+    return;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int bk = bj; bk < bi; ++bk) {
+    const int k0 = bk * kNB;
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      As[r][tx] = (i0 + r < n) ? L[(size_t)(i0 + r) * n + k0 + tx] : 0.0;        // L_{bi, bk}
+      Bs[r][tx] = (j0 + tx < n) ? X[(size_t)(k0 + r) * n + j0 + tx] : 0.0;       // X_{bk, bj}
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int m = 0; m < kNB; ++m) {
+      const double b = Bs[m][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][m], b, acc[q]);
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    Bs[r][tx] = acc[q];                       // T = sum_k L_ik X_kj
+    As[r][tx] = Di[r * kNB + tx];             // Dinv_i (lower)
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    double s = 0.0;
+    for (int m = 0; m <= r; ++m) s = fma(As[r][m], Bs[m][tx], s);
+    if (i0 + r < n && j0 + tx < n) X[(size_t)(i0 + r) * n + j0 + tx] = -s;
   }
 }
 
-// Ainv = L^-T L^-1: Ainv[i][j] = sum_k Xc[i][k] Xc[j][k].
-__global__ void k_xtx(const double* __restrict__ Xc, int n, double* __restrict__ Ainv) {
+// Ainv = X^T X with X = L^-1 lower: Ainv[i][j] = sum_{k >= max(i, j)} X[k][i] X[k][j]. Lower
+// tiles are computed and mirrored, so Ainv is exactly symmetric.
+__global__ void k_xtx(const double* __restrict__ X, int n, double* __restrict__ Ainv) {
   __shared__ double A[16][17], B[16][17];
   const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  if (j0 > i0) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   double s = 0.0;
-  for (int k0 = max(i0, j0) / 16 * 16; k0 < n; k0 += 16) {
-    A[ty][tx] = (i0 + ty < n && k0 + tx < n) ? Xc[(size_t)(i0 + ty) * n + k0 + tx] : 0.0;
-    B[ty][tx] = (j0 + ty < n && k0 + tx < n) ? Xc[(size_t)(j0 + ty) * n + k0 + tx] : 0.0;
+  for (int k0 = i0; k0 < n; k0 += 16) {
+    A[ty][tx] = (k0 + ty < n && i0 + tx < n) ? X[(size_t)(k0 + ty) * n + i0 + tx] : 0.0;
+    B[ty][tx] = (k0 + ty < n && j0 + tx < n) ? X[(size_t)(k0 + ty) * n + j0 + tx] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) s = fma(A[ty][k], B[tx][k], s);
+    for (int k = 0; k < 16; ++k) s = fma(A[k][ty], B[k][tx], s);
     __syncthreads();
   }
-  if (i0 + ty < n && j0 + tx < n) Ainv[(size_t)(i0 + ty) * n + j0 + tx] = s;
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < n && j < n && j <= i) {
+    Ainv[(size_t)i * n + j] = s;
+    Ainv[(size_t)j * n + i] = s;
+  }
 }
 
 }  // namespace rmg

@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kStaticMaxRegions = 4096;
 constexpr long long kStaticMaxComposite = 1LL << 22;                // 4,194,304 nodes
-constexpr size_t kTableBytes = 128 * 1024;                          // >= 4096 * sizeof(RegionDev)
+constexpr size_t kTableBytes = 192 * 1024;                          // region table + dims
 constexpr size_t kStaticBytes = kTableBytes + sizeof(double) * (size_t)kStaticMaxComposite;
 static_assert(sizeof(RegionDev) * kStaticMaxRegions + 3 * sizeof(int) * kStaticMaxRegions <=
                   kTableBytes, "region table does not fit");
@@ -40,7 +40,7 @@ __global__ void k_static_table(int nreg, const int* __restrict__ dims, RegionDev
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int off = 0;
   for (int r = 0; r < nreg; ++r) {
-    tab[r] = RegionDev{dims[3 * r], dims[3 * r + 1], dims[3 * r + 2], 0, off};
+    tab[r] = make_region(dims[3 * r], dims[3 * r + 1], dims[3 * r + 2], off);
     off += dims[3 * r] * dims[3 * r + 1] * dims[3 * r + 2];
   }
 }
