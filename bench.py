@@ -358,7 +358,8 @@ def main():
     e[3].record(stream); torch.cuda.synchronize()
     breakdown = dict(split_ms=e[0].elapsed_time(e[1]), setup_ms=e[1].elapsed_time(e[2]),
                      solve_ms=e[2].elapsed_time(e[3]), layout_ms_once=t_lay * 1e3,
-                     vcycle_launches=hier.vcycle_launches())
+                     vcycle_launches=hier.vcycle_launches(),
+                     tile_shapes=[list(hier.tile_shape(l)) for l in range(cfg["levels"])])
     # V-cycle alone (graph replays), for the per-cycle figure
     r = dp.b.clone()
     z = torch.empty_like(r)

@@ -74,7 +74,17 @@ typedef struct {
   int power_seed_base;   /* start vector of level l: SplitMix64 stream seed_base + l        */
   int precision;         /* rmg_precision                                                  */
   int use_graph;         /* capture the V-cycle in a CUDA graph (1) or launch eagerly (0)  */
+  int tile_shape;        /* stencil-sweep tiles: -1 autotune (default), else a shape index  */
 } rmg_options;
+
+/* Tile shapes of the stencil sweeps (rmg_options.tile_shape, rmg_hier_tile_shape). Every
+ * launch covers all regions of a level with blocks of 256 threads, each block one tile of one
+ * region. Shape 0: runs of 256 consecutive regional nodes. Shapes 1..8: boxes tx x ty x tz of
+ * (32,8,1), (64,4,1), (128,2,1), (16,16,1), (32,4,2), (16,8,2), (16,4,4), (8,8,4); in 2D only
+ * the tz = 1 boxes apply. With -1 the first numeric setup times every applicable shape on
+ * every smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps
+ * the fastest; the choice does not change any result (each node computes the same row). */
+#define RMG_NUM_TILE_SHAPES 9
 
 typedef struct {
   int iterations;        /* products with A (0 when the initial residual already passes)  */
@@ -85,7 +95,7 @@ typedef struct {
 } rmg_solve_info;
 
 /* Defaults: 4 levels, Jacobi, nu1 = nu2 = 2, omega 0.67, degree 3, eig_ratio 20, boost 1.1,
- * 10 power iterations, seed base 10, FP64, graph on. */
+ * 10 power iterations, seed base 10, FP64, graph on, tile shapes autotuned. */
 void rmg_options_default(rmg_options* opts);
 
 /* Create a context on CUDA device `device` that queues work on `cuda_stream`
@@ -313,6 +323,10 @@ rmg_status rmg_hier_level_export(rmg_hier* hier, int level, double* coeffs, doub
                                  int64_t* gids);
 /* Chebyshev lambda~ estimate of a level (host). */
 rmg_status rmg_hier_lambda(rmg_hier* hier, int level, double* lam);
+/* Tile shape the stencil sweeps of a level use (see RMG_NUM_TILE_SHAPES): the box extents, or
+ * 0, 0, 0 for runs of 256 nodes (also for the coarsest level, which is not smoothed). Host
+ * ints; fails with RMG_ERR_ARG for a level outside the hierarchy. */
+rmg_status rmg_hier_tile_shape(rmg_hier* hier, int level, int* tx, int* ty, int* tz);
 /* Coarsest composite matrix restricted to unmasked nodes (dense, row-major, host double
  * [(B*nc)^2], dof cu * B + c) and the composite ids of those nodes (host int64[nc]). Pass NULL
  * to query nc (the number of unmasked composite nodes). */

@@ -50,6 +50,7 @@ void rmg_options_default(rmg_options* o) {
   o->power_seed_base = 10;
   o->precision = RMG_PREC_FP64;
   o->use_graph = 1;
+  o->tile_shape = -1;
 }
 
 rmg_status rmg_create(rmg_ctx** out, int device, void* stream) {
@@ -304,6 +305,15 @@ rmg_status rmg_hier_lambda(rmg_hier* hh, int level, double* lam) {
   Hier& h = hh->h;
   if (level < 0 || level >= h.levels() || level >= 16) return fail(h.layout->ctx, RMG_ERR_ARG, "bad level");
   *lam = h.hsc.lam[level];
+  return RMG_OK;
+}
+
+rmg_status rmg_hier_tile_shape(rmg_hier* hh, int level, int* tx, int* ty, int* tz) {
+  if (!hh || !tx || !ty || !tz) return RMG_ERR_ARG;
+  Hier& h = hh->h;
+  if (level < 0 || level >= h.levels()) return fail(h.layout->ctx, RMG_ERR_ARG, "bad level");
+  if (h.shape[level] < 0) { *tx = *ty = *tz = 0; return RMG_OK; }
+  tile_shape(h, level, tx, ty, tz);
   return RMG_OK;
 }
 

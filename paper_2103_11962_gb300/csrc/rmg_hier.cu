@@ -31,10 +31,10 @@ __global__ void k_convert(size_t n, const S* __restrict__ a, D* __restrict__ b) 
     b[k] = D(a[k]);
 }
 
-__global__ void k_to_bf16(size_t n, const double* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+__global__ void k_to_bf16(size_t n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x)
-    b[k] = __float2bfloat16_rn((float)a[k]);
+    b[k] = __float2bfloat16_rn(a[k]);
 }
 
 // coarse solve: gather the averaged composite right-hand side, x = Abar^-1 rhs, replicate
@@ -204,7 +204,7 @@ struct Exec {
   void stencil(int l, const VT* u, Epi epi) {
     const bool pr = probe && l == 0 && h.probe_ev[0];
     launch_stencil(c(), *h.lv[l], coef(l), u, V(l).y.get(), epi, st, &launches,
-                   pr ? h.probe_ev[0] : nullptr, pr ? h.probe_ev[1] : nullptr);
+                   pr ? h.probe_ev[0] : nullptr, pr ? h.probe_ev[1] : nullptr, h.sweep(l));
     if (pr) probe = false;
   }
 
@@ -470,6 +470,8 @@ void hier_build(Hier& h) {
               RMG_ERR_ARG, "unknown smoother");
   RMG_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, RMG_ERR_ARG, "cheb_degree in [1, 8]");
   RMG_REQUIRE(o.precision >= 0 && o.precision <= 2, RMG_ERR_ARG, "unknown precision");
+  RMG_REQUIRE(o.tile_shape >= -1 && o.tile_shape < kNumTileShapes, RMG_ERR_ARG,
+              "tile_shape must be -1 (autotune) or a shape index");
   RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1 &&
               o.power_iters <= 100, RMG_ERR_ARG, "bad Chebyshev options");
   h.lv.push_back(&h.layout->L0);
@@ -481,6 +483,9 @@ void hier_build(Hier& h) {
   const int Lv = h.levels();
   h.stored.assign(Lv, 0);
   h.pw.resize(Lv);
+  h.shape.assign(Lv, -1);
+  h.stiles.resize(Lv);
+  h.sgrid.resize(Lv);
   h.v64.resize(Lv);
   for (int l = 0; l < Lv; ++l) {
     const size_t nb = (size_t)h.lv[l]->B * h.lv[l]->n_r;
@@ -493,8 +498,10 @@ void hier_build(Hier& h) {
       Level& L = *h.lv[l];
       h.v32[l].alloc(L.B * L.n_r);
       L.dinv32.ensure((size_t)L.B * L.n_r);
-      if (o.precision == RMG_PREC_FP32) L.coef32.ensure((size_t)L.B * L.B * L.kind * L.n_r);
-      else L.coef16.ensure((size_t)L.B * L.B * L.kind * L.n_r);
+      // FP32 coefficients on every level of a mixed hierarchy (the FP32 Galerkin chain runs
+      // on them); the BF16 cycle reads its own copy
+      L.coef32.ensure((size_t)L.B * L.B * L.kind * L.n_r);
+      if (o.precision == RMG_PREC_FP32_BF16COEF) L.coef16.ensure((size_t)L.B * L.B * L.kind * L.n_r);
     }
   }
   if (Lv > 1) h.layout->apbuf.ensure((size_t)(h.lv[0]->dim == 3 ? 27 : 9) * h.lv[0]->n_r);
@@ -526,6 +533,7 @@ void hier_build(Hier& h) {
   RMG_LAUNCHED();
   const size_t nd = (size_t)std::max(1LL, ncd);
   h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd); h.Linv.alloc(nd * nd);
+  h.Tinv.alloc(nd * nd);
   h.Dblk.alloc((size_t)((nd + kNB - 1) / kNB) * kNB * kNB);
   h.xc.alloc(nd); h.rc.alloc(nd);
   RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
@@ -555,38 +563,39 @@ static void compute_dinv(Hier& h, Level& L) {
   }
 }
 
-static void galerkin(Hier& h, int l, const Level& F, Level& C) {
+template <typename T>
+static void galerkin_t(Hier& h, int l, const Level& F, Level& C, const T* fcoef, T* ccoef) {
   Ctx& c = *h.c;
-  double* ap = h.layout->apbuf.get();
+  T* ap = reinterpret_cast<T*>(h.layout->apbuf.get());
   const Grid Gf = F.grid(), Gc = C.grid();
   const int gf = persistent_grid(c, Gf.ntiles), gc = persistent_grid(c, Gc.ntiles);
   // (P x I)^T A (P x I) of a B x B block operator is the scalar product on every block; a
   // masked coarse row is the identity row in the diagonal blocks and zero elsewhere
   for (int blk = 0; blk < F.B * F.B; ++blk) {
-  const double* fco = F.coef.get() + (size_t)blk * F.kind * F.n_r;
-  double* cco = C.coef.get() + (size_t)blk * C.kind * C.n_r;
+  const T* fco = fcoef + (size_t)blk * F.kind * F.n_r;
+  T* cco = ccoef + (size_t)blk * C.kind * C.n_r;
   const double mdiag = (blk / F.B == blk % F.B) ? 1.0 : 0.0;
 #define RMG_RAP(FK, CK, D)                                                                    \
   {                                                                                           \
-    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
-    RMG_CUDA(cudaFuncSetAttribute(k_ap<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(T);                         \
+    RMG_CUDA(cudaFuncSetAttribute(k_ap<FK, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   smem));                                                     \
-    k_ap<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, F.mask.get(),        \
+    k_ap<FK, D, T><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, F.mask.get(),        \
                                                C.mask.get(), ap);                             \
   }                                                                                           \
   RMG_LAUNCHED();                                                                             \
-  k_rtap<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, C.mask.get(),     \
+  k_rtap<CK, D, T><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, C.mask.get(),     \
                                             C.mult.get(), mdiag, cco)
 #define RMG_RAPW(FK, CK, D)                                                                   \
   {                                                                                           \
-    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(double);                         \
-    RMG_CUDA(cudaFuncSetAttribute(k_ap_w<FK, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(T);                         \
+    RMG_CUDA(cudaFuncSetAttribute(k_ap_w<FK, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                   smem));                                                     \
-    k_ap_w<FK, D><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, h.pw[l].get(),       \
+    k_ap_w<FK, D, T><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, h.pw[l].get(),       \
                                                  F.mask.get(), C.mask.get(), ap);             \
   }                                                                                           \
   RMG_LAUNCHED();                                                                             \
-  k_rtap_w<CK, D><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, h.pw[l].get(),   \
+  k_rtap_w<CK, D, T><<<gc, kTile, 0, c.stream>>>(Gc, F.regions.get(), ap, F.n_r, h.pw[l].get(),   \
                                               C.mask.get(), C.mult.get(), mdiag, cco)
   if (h.stored[l]) {
     switch (F.kind) {
@@ -607,6 +616,21 @@ static void galerkin(Hier& h, int l, const Level& F, Level& C) {
   }
 #undef RMG_RAP
 #undef RMG_RAPW
+}
+
+// Level l + 1 = Galerkin product of level l: in FP64 for the plain method; for a mixed
+// hierarchy in FP32 on the FP32 coefficients, then widened to FP64 (exactly) for the dense
+// coarse solve, the diagonal and introspection.
+static void galerkin(Hier& h, int l, Level& F, Level& C) {
+  if (!h.mixed()) {
+    galerkin_t<double>(h, l, F, C, F.coef.get(), C.coef.get());
+    return;
+  }
+  galerkin_t<float>(h, l, F, C, F.coef32.get(), C.coef32.get());
+  const size_t nco = (size_t)C.B * C.B * C.kind * C.n_r;
+  const int g = persistent_grid(*h.c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
+  k_convert<float, double><<<g, 256, 0, h.c->stream>>>(nco, C.coef32.get(), C.coef.get());
+  RMG_LAUNCHED();
 }
 
 // Stored transfer weights for level -> level+1 (NULL restores linear interpolation). The
@@ -699,11 +723,13 @@ static void power_method_t(Hier& h, int l) {
   VT* a = V.u.get();
   VT* b = V.r.get();
   for (int it = 0; it < h.o.power_iters; ++it) {
-    launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr);
+    launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr, nullptr,
+                   nullptr, h.sweep(l));
     std::swap(a, b);
     if (sizeof(VT) < 8 && (it + 1) % 8 == 0 && it + 1 < h.o.power_iters) normalise(a);
   }
-  launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr);
+  launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr, nullptr,
+                 nullptr, h.sweep(l));
   dot_t<VT>(c, n, L.n_r, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
   dot_t<VT>(c, n, L.n_r, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
   k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
@@ -757,11 +783,17 @@ static void coarse_factor(Hier& h) {
     }
   }
   c.check_device_error("rmg_setup (coarse factorisation)");
-  // X = L^-1 block row by block row, then Ainv = X^T X
+  // X = L^-1 by recursive doubling from the inverted diagonal blocks, then Ainv = X^T X
   RMG_CUDA(cudaMemsetAsync(h.Linv.get(), 0, (size_t)nc * nc * sizeof(double), st));
   const int nblk = (nc + kNB - 1) / kNB;
-  for (int bi = 0; bi < nblk; ++bi) {
-    k_trinv_row<<<bi + 1, 256, 0, st>>>(h.Mfac.get(), nc, bi, h.Dblk.get(), h.Linv.get());
+  k_inv_diag_blocks<<<nblk, 256, 0, st>>>(nc, h.Dblk.get(), h.Linv.get());
+  RMG_LAUNCHED();
+  for (int s = kNB; s < nc; s *= 2) {
+    const int tiles = (s + kNB - 1) / kNB, pairs = (nc + 2 * s - 1) / (2 * s);
+    const dim3 grid(tiles, tiles, pairs);
+    k_inv_merge<1><<<grid, 256, 0, st>>>(h.Mfac.get(), h.Linv.get(), h.Tinv.get(), nc, s);
+    RMG_LAUNCHED();
+    k_inv_merge<2><<<grid, 256, 0, st>>>(h.Mfac.get(), h.Linv.get(), h.Tinv.get(), nc, s);
     RMG_LAUNCHED();
   }
   const int t = (nc + 15) / 16;
@@ -769,21 +801,138 @@ static void coarse_factor(Hier& h) {
   RMG_LAUNCHED();
 }
 
+// FP32 copy of the level-0 coefficients for the mixed hierarchy's FP32 Galerkin chain.
+static void level0_to_fp32(Hier& h) {
+  Ctx& c = *h.c;
+  Level& L = *h.lv[0];
+  const size_t nco = (size_t)L.B * L.B * L.kind * L.n_r;
+  const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
+  k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
+  RMG_LAUNCHED();
+}
+
+// The mixed cycle's remaining copies: FP32 D~^-1 on every level and, for the BF16 variant, the
+// BF16 coefficients (from the FP32 ones).
 static void make_low_precision(Hier& h) {
   Ctx& c = *h.c;
   for (int l = 0; l < h.levels(); ++l) {
     Level& L = *h.lv[l];
     const size_t nco = (size_t)L.B * L.B * L.kind * L.n_r;
     const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
-    if (h.o.precision == RMG_PREC_FP32)
-      k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
-    else
-      k_to_bf16<<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef16.get());
-    RMG_LAUNCHED();
+    if (h.o.precision == RMG_PREC_FP32_BF16COEF) {
+      k_to_bf16<<<g, 256, 0, c.stream>>>(nco, L.coef32.get(), L.coef16.get());
+      RMG_LAUNCHED();
+    }
     k_convert<double, float><<<g, 256, 0, c.stream>>>((size_t)L.B * L.n_r, L.dinv.get(),
                                                       L.dinv32.get());
     RMG_LAUNCHED();
   }
+}
+
+// ---------------------------------------------------------------------- tile-shape autotuner
+// Candidate tile shapes of the stencil sweeps: index 0 = runs of kTile consecutive nodes,
+// 1.. = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty). Boxes hand every
+// thread its (i, j, l) without a decode and keep stencil neighbours inside the block, at the
+// price of idle threads where a box overhangs the region; which wins depends on the region
+// sizes, the stencil and the precision, so each hierarchy times them.
+
+static bool shape_fits(const Level& L, int k) {
+  const TileShape t = kTileShapes[k];
+  if (t.lx < 0) return true;
+  if (L.dim == 2 && t.lx + t.ly != 8) return false;      // 2D levels need tz = 1
+  for (int d : L.hdims)
+    if (d >= 32768) return false;                         // box corners are 16-bit
+  return true;
+}
+
+static void set_shape(Hier& h, int l, int k) {
+  Level& L = *h.lv[l];
+  h.shape[l] = k;
+  const TileShape t = kTileShapes[k];
+  if (t.lx < 0) {
+    h.sgrid[l] = L.grid();
+    return;
+  }
+  const int tx = 1 << t.lx, ty = 1 << t.ly, tz = kTile >> (t.lx + t.ly);
+  std::vector<Tile> tl;
+  for (int r = 0; r < L.nreg; ++r) {
+    const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1], nz = L.hdims[3 * r + 2];
+    for (int z = 0; z < nz; z += tz)
+      for (int y = 0; y < ny; y += ty)
+        for (int x = 0; x < nx; x += tx)
+          tl.push_back(Tile{r, 0, (short)x, (short)y, (short)z, 0});
+  }
+  h.stiles[l].alloc(tl.size());
+  RMG_CUDA(cudaMemcpy(h.stiles[l].get(), tl.data(), tl.size() * sizeof(Tile),
+                      cudaMemcpyHostToDevice));
+  Grid G = L.grid();
+  G.tiles = h.stiles[l].get();
+  G.ntiles = (int)tl.size();
+  G.lx = t.lx;
+  G.ly = t.ly;
+  h.sgrid[l] = G;
+}
+
+// Time the candidate shapes on every smoothed level with the residual sweep in the cycle's
+// precision (3 launches after a warm-up, CUDA events on the library stream) and keep the
+// fastest; tile_shape >= 0 in the options forces one shape where it fits.
+template <typename VT, typename CT>
+static void autotune_t(Hier& h) {
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  Exec<VT, CT> ex(h, st);
+  cudaEvent_t e0, e1;
+  RMG_CUDA(cudaEventCreate(&e0));
+  RMG_CUDA(cudaEventCreate(&e1));
+  for (int l = 0; l + 1 < h.levels(); ++l) {
+    const Level& L = *h.lv[l];
+    LevelVecs<VT>& V = ex.V(l);
+    const size_t nv = (size_t)L.B * L.n_r;
+    RMG_CUDA(cudaMemsetAsync(V.u.get(), 0, nv * sizeof(VT), st));
+    RMG_CUDA(cudaMemsetAsync(V.b.get(), 0, nv * sizeof(VT), st));
+    if (h.o.tile_shape >= 0) {
+      set_shape(h, l, shape_fits(L, h.o.tile_shape) ? h.o.tile_shape : 0);
+      continue;
+    }
+    int best = 0;
+    float best_ms = 0.f;
+    for (int k = 0; k < kNumTileShapes; ++k) {
+      if (!shape_fits(L, k)) continue;
+      set_shape(h, l, k);
+      auto run = [&]() {
+        launch_stencil(c, L, ex.coef(l), (const VT*)V.u.get(), V.y.get(),
+                       EpiResid<VT>{V.b.get(), V.r.get()}, st, nullptr, nullptr, nullptr,
+                       &h.sgrid[l]);
+      };
+      run();
+      RMG_CUDA(cudaEventRecord(e0, st));
+      for (int rep = 0; rep < 3; ++rep) run();
+      RMG_CUDA(cudaEventRecord(e1, st));
+      RMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      RMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (k == 0 || ms < best_ms) { best = k; best_ms = ms; }
+    }
+    set_shape(h, l, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+static void autotune(Hier& h) {
+  switch (h.o.precision) {
+    case RMG_PREC_FP64: autotune_t<double, double>(h); break;
+    case RMG_PREC_FP32: autotune_t<float, float>(h); break;
+    default: autotune_t<float, __nv_bfloat16>(h); break;
+  }
+  h.tuned = true;
+}
+
+void tile_shape(const Hier& h, int l, int* tx, int* ty, int* tz) {
+  const TileShape t = kTileShapes[h.shape[l]];
+  *tx = t.lx < 0 ? 0 : 1 << t.lx;
+  *ty = t.lx < 0 ? 0 : 1 << t.ly;
+  *tz = t.lx < 0 ? 0 : kTile >> (t.lx + t.ly);
 }
 
 void hier_numeric(Hier& h) {
@@ -798,12 +947,14 @@ void hier_numeric(Hier& h) {
   h.kind0 = L0.kind;
   h.coef0 = L0.coef.get();
   compute_dinv(h, *h.lv[0]);
+  if (h.mixed()) level0_to_fp32(h);
   for (int l = 0; l + 1 < Lv; ++l) {
     galerkin(h, l, *h.lv[l], *h.lv[l + 1]);
     compute_dinv(h, *h.lv[l + 1]);
   }
   // the mixed cycle's coefficient copies first: its power method runs on them
   if (h.mixed()) make_low_precision(h);
+  if (!h.tuned) autotune(h);
   if (h.o.smoother == RMG_SMOOTHER_CHEBYSHEV)
     for (int l = 0; l + 1 < Lv; ++l) power_method(h, l);
   coarse_factor(h);

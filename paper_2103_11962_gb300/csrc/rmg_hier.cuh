@@ -16,6 +16,14 @@ struct LevelVecs {
   }
 };
 
+// Stencil-sweep tile shapes (index 0: runs of kTile consecutive nodes; 1..: boxes
+// 2^lx x 2^ly x kTile / 2^(lx + ly)), in the order rmg_options.tile_shape numbers them.
+struct TileShape { int lx, ly; };
+constexpr TileShape kTileShapes[] = {{-1, 0}, {5, 3}, {6, 2}, {7, 1}, {4, 4},
+                                     {5, 2}, {4, 3}, {4, 2}, {3, 3}};
+constexpr int kNumTileShapes = (int)(sizeof(kTileShapes) / sizeof(kTileShapes[0]));
+static_assert(kNumTileShapes == RMG_NUM_TILE_SHAPES, "tile shape table and header disagree");
+
 struct Hier {
   rmg_layout* layout = nullptr;
   Ctx* c = nullptr;
@@ -31,7 +39,7 @@ struct Hier {
   DBuf<int> cidx, cu2slot;
   DBuf<long long> cu2gid;
   DBuf<double> Mfac, X, Ainv, xc, rc;
-  DBuf<double> Linv, Dblk;                   // L^-1 and the inverted 32 x 32 diagonal blocks
+  DBuf<double> Linv, Dblk, Tinv;             // L^-1, inverted 32 x 32 diagonal blocks, scratch
   // graph of one V-cycle
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -43,6 +51,11 @@ struct Hier {
   std::vector<char> stored;
   std::vector<DBuf<float>> pw;
   std::vector<char> graph_stored;            // stored-transfer flags the graph was captured with
+  // stencil-sweep tiles per level (autotuned shape; see kTileShapes): shape index and grid
+  std::vector<int> shape;
+  std::vector<DBuf<Tile>> stiles;
+  std::vector<Grid> sgrid;
+  bool tuned = false;
   int kind0 = 0;                             // level-0 stencil and buffer seen by the graph
   const double* coef0 = nullptr;
   // probe: CUDA events around one level-0 smoother stencil launch of every V-cycle
@@ -59,11 +72,16 @@ struct Hier {
 
   ~Hier();
   int levels() const { return (int)lv.size(); }
+  // tuned stencil-sweep grid of level l, or null (the level's run tiles) before tuning
+  const Grid* sweep(int l) const {
+    return l < (int)shape.size() && shape[l] >= 0 ? &sgrid[l] : nullptr;
+  }
   bool mixed() const { return o.precision != RMG_PREC_FP64; }
 };
 
 void hier_build(Hier& h);          // symbolic: coarse layouts, buffers
-void hier_numeric(Hier& h);        // numeric: diagonals, RAP, lambda, coarse factor, graph
+void hier_numeric(Hier& h);
+void tile_shape(const Hier& h, int level, int* tx, int* ty, int* tz);        // numeric: diagonals, RAP, lambda, coarse factor, graph
 void probe_collect(Hier& h);       // read the probe events of the last V-cycle
 void vcycle(Hier& h);              // lv[0] rhs in v64[0].b (or v32[0].b) -> result in .u
 void vcycle_apply(Hier& h, const double* r, double* z, int regional);

@@ -142,9 +142,12 @@ __host__ __device__ inline RegionDev make_region(int nx, int ny, int nz, int off
                    fast ? 1.0f / (float)ny : 0.0f};
 }
 
-struct Tile {   // a run of up to kTile consecutive nodes of one region
+// A tile of one region: in run mode (Grid::lx < 0) up to kTile consecutive nodes from `start`;
+// in box mode a tx x ty x tz box of nodes with corner (x0, y0, z0), tx * ty * tz = kTile.
+struct Tile {
   int region;
-  int start;   // local start inside the region
+  int start;              // run mode: local start inside the region
+  short x0, y0, z0, pad;  // box mode: corner of the box
 };
 
 constexpr int kTile = 256;
@@ -156,6 +159,7 @@ struct Grid {
   int ntiles;
   int nreg;
   int n_r;
+  int lx = -1, ly = 0;    // box mode: tx = 2^lx, ty = 2^ly, tz = kTile / (tx ty); lx < 0: runs
 };
 
 struct Ctx;
@@ -192,7 +196,7 @@ struct Level {
   DBuf<__nv_bfloat16> coef16;
   DBuf<float> dinv32;
 
-  Grid grid() const { return Grid{regions.get(), tiles.get(), (int)htiles.size(), nreg, n_r}; }
+  Grid grid() const { return Grid{regions.get(), tiles.get(), (int)htiles.size(), nreg, n_r, -1, 0}; }
 };
 
 // Device-resident scalars of the solver (no host round trip inside a V-cycle or a CG step).

@@ -2,7 +2,8 @@
 //
 // Every node-parallel kernel is a persistent grid-stride loop over a tile list that covers
 // all regions of a level (one launch batches all regions, whatever their sizes). A tile is a
-// run of up to kTile consecutive nodes of one region; blockDim.x == kTile.
+// run of up to kTile consecutive nodes of one region, or, for the stencil sweeps, a box of
+// kTile nodes whose shape the hierarchy picks by timing (autotuned); blockDim.x == kTile.
 //
 // The interface summation Psi^T Psi (Sec. 3.1) is split in two phases. Phase A applies the
 // region stencil at every node; a node with a single copy finishes its update at once, a
@@ -58,9 +59,22 @@ __device__ __forceinline__ int region_of(const RegionDev* R, int nreg, int n) {
   for (int t_ = blockIdx.x; t_ < (G).ntiles; t_ += gridDim.x) {                \
     const Tile tile_ = (G).tiles[t_];                                          \
     const RegionDev R = (G).regions[tile_.region];                             \
-    const int li = tile_.start + (int)threadIdx.x;                             \
-    if (li >= R.nx * R.ny * R.nz) continue;                                    \
+    int li, bi_ = -1, bj_ = 0, bl_ = 0;                                        \
+    if ((G).lx < 0) {                                                          \
+      li = tile_.start + (int)threadIdx.x;                                     \
+      if (li >= R.nx * R.ny * R.nz) continue;                                  \
+    } else {                                                                   \
+      bi_ = tile_.x0 + ((int)threadIdx.x & ((1 << (G).lx) - 1));               \
+      bj_ = tile_.y0 + (((int)threadIdx.x >> (G).lx) & ((1 << (G).ly) - 1));   \
+      bl_ = tile_.z0 + ((int)threadIdx.x >> ((G).lx + (G).ly));                \
+      if (bi_ >= R.nx || bj_ >= R.ny || bl_ >= R.nz) continue;                 \
+      li = bi_ + R.nx * (bj_ + R.ny * bl_);                                    \
+    }                                                                          \
     const int n = R.off + li;
+
+// (i, j, l) of the current node inside RMG_FOR_NODES: from the box in box mode, else decoded.
+#define RMG_DECODE(i, j, l)                                                    \
+  if (bi_ >= 0) { i = bi_; j = bj_; l = bl_; } else decode(li, R, i, j, l);
 
 #define RMG_END_FOR_NODES }
 
@@ -101,7 +115,7 @@ k_stencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
           const uint8_t* __restrict__ mult, AT* __restrict__ y, Epi epi) {
   RMG_FOR_NODES(G)
     int i, j, l;
-    decode(li, R, i, j, l);
+    RMG_DECODE(i, j, l);
     const AT au = stencil_row<KIND, CT, VT, AT>(coef, u, n, G.n_r, i, j, l, R);
     if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
   RMG_END_FOR_NODES
@@ -133,7 +147,7 @@ k_bstencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
   using S = Sten<KIND>;
   RMG_FOR_NODES(G)
     int i, j, l;
-    decode(li, R, i, j, l);
+    RMG_DECODE(i, j, l);
     AT au[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) au[c] = AT(0);
@@ -288,6 +302,13 @@ __host__ __device__ constexpr double w1d(int a) {
 __host__ __device__ constexpr double wrem(int rem, int side) {
   return rem == 0 ? (side == 0 ? 1.0 : 0.0)
        : side == 1 ? rem / 3.0 : 1.0 - rem / 3.0;
+}
+// The same weights as compile-time constants in precision T (selects only, no division).
+template <typename T>
+__host__ __device__ constexpr T wrem_t(int rem, int side) {
+  return rem == 0 ? (side == 0 ? T(1) : T(0))
+       : rem == 1 ? (side == 1 ? T(wrem(1, 1)) : T(wrem(1, 0)))
+                  : (side == 1 ? T(wrem(2, 1)) : T(wrem(2, 0)));
 }
 
 // Region-local restriction w = [[R]] rs for every coarse node, rs = r / mult being the

@@ -15,11 +15,12 @@ void launch_groups(Ctx& c, const Level& L, const AT* y, Epi epi, cudaStream_t st
   RMG_LAUNCHED();
 }
 
+// Phase A over `sweep` (a tuned tile list of L; the level's run tiles when null), then phase B.
 template <class Epi, typename CT, typename VT, typename AT>
 void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
                     cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
-                    cudaEvent_t ev1 = nullptr) {
-  const Grid G = L.grid();
+                    cudaEvent_t ev1 = nullptr, const Grid* sweep = nullptr) {
+  const Grid G = sweep ? *sweep : L.grid();
   const int gb = persistent_grid(c, G.ntiles);
   // external record nodes when capturing, so the events can be timed after a graph replay
   if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));

@@ -194,7 +194,7 @@ void build_tiles(Level& L) {
   L.htiles.clear();
   for (int r = 0; r < L.nreg; ++r) {
     const int sz = L.hdims[3 * r] * L.hdims[3 * r + 1] * L.hdims[3 * r + 2];
-    for (int s = 0; s < sz; s += kTile) L.htiles.push_back(Tile{r, s});
+    for (int s = 0; s < sz; s += kTile) L.htiles.push_back(Tile{r, s, 0, 0, 0, 0});
   }
   L.tiles.alloc(L.htiles.size());
   RMG_CUDA(cudaMemcpy(L.tiles.get(), L.htiles.data(), L.htiles.size() * sizeof(Tile),

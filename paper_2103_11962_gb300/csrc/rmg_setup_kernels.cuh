@@ -71,27 +71,31 @@ struct EpiRecip {
 //     support of P(f, C) ap[.][f]; the weights P(f, C) are compile-time constants.
 // Masked fine nodes have zero rows of P, masked coarse nodes zero columns; a masked coarse
 // row becomes 1/mult on the diagonal so that the composite sum is the identity row.
+// T is the arithmetic of the product: FP64 for the plain method; FP32 for the hierarchies of
+// the mixed-precision cycle, whose coarse operators only ever enter an FP32 cycle (GB300's
+// FP64 pipe would make these sums the largest part of the setup).
 __device__ __forceinline__ int floor_div3m1(int x) { return (x + 2) / 3 - 1; }   // (x-1) div 3, x >= 0
 
-template <int FK, int DIM>
+template <int FK, int DIM, typename T>
 __global__ void __launch_bounds__(kTile)
-k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fcoef,
+k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const T* __restrict__ fcoef,
      const uint8_t* __restrict__ fmask, const uint8_t* __restrict__ cmask,
-     double* __restrict__ ap) {
+     T* __restrict__ ap) {
   using FS = Sten<FK>;
   constexpr int NO = DIM == 3 ? 27 : 9;
-  __shared__ double tab[27 * 8];
-  extern __shared__ double ap_acc[];                 // NO x kTile accumulators (dynamic)
-  double (*acc)[kTile] = reinterpret_cast<double (*)[kTile]>(ap_acc);
+  __shared__ T tab[27 * 8];
+  extern __shared__ __align__(16) unsigned char ap_smem[];   // NO x kTile accumulators
+  T (*acc)[kTile] = reinterpret_cast<T (*)[kTile]>(ap_smem);
   for (int e = threadIdx.x; e < 27 * 8; e += blockDim.x) {
     const int r = e >> 3, combo = e & 7;
-    tab[e] = wrem(r / 9, combo >> 2) * (wrem((r / 3) % 3, (combo >> 1) & 1) * wrem(r % 3, combo & 1));
+    tab[e] = wrem_t<T>(r / 9, combo >> 2) *
+             (wrem_t<T>((r / 3) % 3, (combo >> 1) & 1) * wrem_t<T>(r % 3, combo & 1));
   }
   __syncthreads();
   const int tid = threadIdx.x;
   RMG_FOR_NODES(Gf)
 #pragma unroll
-    for (int o = 0; o < NO; ++o) acc[o][tid] = 0.0;
+    for (int o = 0; o < NO; ++o) acc[o][tid] = T(0);
     if (!fmask[n]) {
       int x, y, z;
       decode(li, R, x, y, z);
@@ -101,13 +105,13 @@ k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fc
       for (int s = 0; s < FS::S; ++s) {
         const int gx = x + FS::dx(s), gy = y + FS::dy(s), gz = z + FS::dz(s);
         if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
-        const double v = fcoef[(size_t)s * Gf.n_r + n];
-        if (v == 0.0) continue;
+        const T v = fcoef[(size_t)s * Gf.n_r + n];
+        if (v == T(0)) continue;
         if (fmask[R.off + gx + R.nx * (gy + R.ny * gz)]) continue;
         const int x0 = gx / 3, rx = gx - 3 * x0;
         const int y0 = gy / 3, ry = gy - 3 * y0;
         const int z0 = DIM == 3 ? gz / 3 : 0, rz = DIM == 3 ? gz - 3 * z0 : 0;
-        const double* t = tab + 8 * (rx + 3 * ry + 9 * rz);
+        const T* t = tab + 8 * (rx + 3 * ry + 9 * rz);
         for (int c = 0; c < (rz ? 2 : 1); ++c)
           for (int b = 0; b < (ry ? 2 : 1); ++b)
             for (int a = 0; a < (rx ? 2 : 1); ++a) {
@@ -123,10 +127,10 @@ k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fc
   RMG_END_FOR_NODES
 }
 
-template <int DIM, bool CHECK, bool STORED>
-__device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r,
+template <int DIM, bool CHECK, bool STORED, typename T>
+__device__ __forceinline__ void rtap_sum(const T* __restrict__ ap, int fn_r,
                                          const RegionDev& F, const float* __restrict__ wr,
-                                         int I, int J, int L, double (&acc)[27]) {
+                                         int I, int J, int L, T (&acc)[27]) {
   constexpr int ZL = DIM == 3 ? -2 : 0, ZH = DIM == 3 ? 2 : 0;
 #pragma unroll
   for (int c = ZL; c <= ZH; ++c) {
@@ -141,13 +145,13 @@ __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r
         const int fx = 3 * I + a;
         if (CHECK && (fx < 0 || fx >= F.nx)) continue;
         const int f = F.off + fx + F.nx * (fy + F.ny * fz);
-        double wf;
+        T wf;
         if (STORED) {
           const float wz = DIM == 3 ? pw_seen_from_coarse<float>(wr, fn_r, f, 2, c) : 1.f;
-          wf = (double)(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
-                              pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
+          wf = T(wz * (pw_seen_from_coarse<float>(wr, fn_r, f, 1, b) *
+                       pw_seen_from_coarse<float>(wr, fn_r, f, 0, a)));
         } else {
-          wf = (DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a));
+          wf = T((DIM == 3 ? w1d(c) : 1.0) * (w1d(b) * w1d(a)));   // compile-time constant
         }
         // ap of node f is stored relative to the coarse node (f - 1) div 3 on each axis,
         // which is C - 1 for offsets a <= 0 and C for a >= 1
@@ -172,26 +176,26 @@ __device__ __forceinline__ void rtap_sum(const double* __restrict__ ap, int fn_r
   }
 }
 
-template <int CK, int DIM>
+template <int CK, int DIM, typename T>
 __global__ void __launch_bounds__(kTile)
-k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
+k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const T* __restrict__ ap, int fn_r,
        const uint8_t* __restrict__ cmask, const uint8_t* __restrict__ cmult, double mdiag,
-       double* __restrict__ ccoef) {
+       T* __restrict__ ccoef) {
   using CS = Sten<CK>;
   RMG_FOR_NODES(Gc)
-    double acc[27];
+    T acc[27];
 #pragma unroll
-    for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+    for (int o = 0; o < 27; ++o) acc[o] = T(0);
     if (cmask[n]) {
-      acc[DIM == 3 ? 13 : 4] = mdiag / (double)cmult[n];
+      acc[DIM == 3 ? 13 : 4] = T(mdiag) / T(cmult[n]);
     } else {
       int I, J, L;
       decode(li, R, I, J, L);
       const RegionDev F = fregs[tile_.region];
       const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
                          (DIM == 2 || (L > 0 && L < R.nz - 1));
-      if (inner) rtap_sum<DIM, false, false>(ap, fn_r, F, nullptr, I, J, L, acc);
-      else rtap_sum<DIM, true, false>(ap, fn_r, F, nullptr, I, J, L, acc);
+      if (inner) rtap_sum<DIM, false, false, T>(ap, fn_r, F, nullptr, I, J, L, acc);
+      else rtap_sum<DIM, true, false, T>(ap, fn_r, F, nullptr, I, J, L, acc);
     }
 #pragma unroll
     for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
@@ -199,19 +203,19 @@ k_rtap(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ 
 }
 
 // Galerkin product with stored per-node weights (same two steps as k_ap / k_rtap).
-template <int FK, int DIM>
+template <int FK, int DIM, typename T>
 __global__ void __launch_bounds__(kTile)
-k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ fcoef,
+k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const T* __restrict__ fcoef,
        const float* __restrict__ wr, const uint8_t* __restrict__ fmask,
-       const uint8_t* __restrict__ cmask, double* __restrict__ ap) {
+       const uint8_t* __restrict__ cmask, T* __restrict__ ap) {
   using FS = Sten<FK>;
   constexpr int NO = DIM == 3 ? 27 : 9;
-  extern __shared__ double ap_acc[];
-  double (*acc)[kTile] = reinterpret_cast<double (*)[kTile]>(ap_acc);
+  extern __shared__ __align__(16) unsigned char ap_smem[];
+  T (*acc)[kTile] = reinterpret_cast<T (*)[kTile]>(ap_smem);
   const int tid = threadIdx.x;
   RMG_FOR_NODES(Gf)
 #pragma unroll
-    for (int o = 0; o < NO; ++o) acc[o][tid] = 0.0;
+    for (int o = 0; o < NO; ++o) acc[o][tid] = T(0);
     if (!fmask[n]) {
       int x, y, z;
       decode(li, R, x, y, z);
@@ -221,8 +225,8 @@ k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ 
       for (int s = 0; s < FS::S; ++s) {
         const int gx = x + FS::dx(s), gy = y + FS::dy(s), gz = z + FS::dz(s);
         if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
-        const double v = fcoef[(size_t)s * Gf.n_r + n];
-        if (v == 0.0) continue;
+        const T v = fcoef[(size_t)s * Gf.n_r + n];
+        if (v == T(0)) continue;
         const int f2 = R.off + gx + R.nx * (gy + R.ny * gz);
         if (fmask[f2]) continue;
         const int x0 = gx / 3, rx = gx - 3 * x0;
@@ -238,7 +242,7 @@ k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ 
               if (cmask[C.off + X + C.nx * (Y + C.ny * Z)]) continue;
               const float wgt = (c ? wz : 1.f - wz) * ((b ? wy : 1.f - wy) * (a ? wx : 1.f - wx));
               const int o = (X - cx0) + 3 * (Y - cy0) + 9 * (Z - cz0);
-              acc[o][tid] = fma(v, (double)wgt, acc[o][tid]);
+              acc[o][tid] = fma(v, T(wgt), acc[o][tid]);
             }
       }
     }
@@ -247,26 +251,26 @@ k_ap_w(Grid Gf, const RegionDev* __restrict__ cregs, const double* __restrict__ 
   RMG_END_FOR_NODES
 }
 
-template <int CK, int DIM>
+template <int CK, int DIM, typename T>
 __global__ void __launch_bounds__(kTile)
-k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const double* __restrict__ ap, int fn_r,
+k_rtap_w(Grid Gc, const RegionDev* __restrict__ fregs, const T* __restrict__ ap, int fn_r,
          const float* __restrict__ wr, const uint8_t* __restrict__ cmask,
-         const uint8_t* __restrict__ cmult, double mdiag, double* __restrict__ ccoef) {
+         const uint8_t* __restrict__ cmult, double mdiag, T* __restrict__ ccoef) {
   using CS = Sten<CK>;
   RMG_FOR_NODES(Gc)
-    double acc[27];
+    T acc[27];
 #pragma unroll
-    for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+    for (int o = 0; o < 27; ++o) acc[o] = T(0);
     if (cmask[n]) {
-      acc[DIM == 3 ? 13 : 4] = mdiag / (double)cmult[n];
+      acc[DIM == 3 ? 13 : 4] = T(mdiag) / T(cmult[n]);
     } else {
       int I, J, L;
       decode(li, R, I, J, L);
       const RegionDev F = fregs[tile_.region];
       const bool inner = I > 0 && I < R.nx - 1 && J > 0 && J < R.ny - 1 &&
                          (DIM == 2 || (L > 0 && L < R.nz - 1));
-      if (inner) rtap_sum<DIM, false, true>(ap, fn_r, F, wr, I, J, L, acc);
-      else rtap_sum<DIM, true, true>(ap, fn_r, F, wr, I, J, L, acc);
+      if (inner) rtap_sum<DIM, false, true, T>(ap, fn_r, F, wr, I, J, L, acc);
+      else rtap_sum<DIM, true, true, T>(ap, fn_r, F, wr, I, J, L, acc);
     }
 #pragma unroll
     for (int s = 0; s < CS::S; ++s) ccoef[(size_t)s * Gc.n_r + n] = acc[s];
@@ -469,7 +473,7 @@ __global__ void k_coarse_assemble(int ncomp, int B, const RegionDev* __restrict_
 //  k_chol_diag   one warp factors the 32 x 32 diagonal block and inverts it (Dinv_k = L_kk^-1);
 //  k_chol_panel  L_ik = A_ik L_kk^-T as a product with Dinv_k (no serial solve per row);
 //  k_chol_update trailing update of the lower triangle;
-//  k_trinv_row   block row i of X = L^-1: X_ij = -Dinv_i sum_{k=j}^{i-1} L_ik X_kj, X_ii = Dinv_i;
+//  k_inv_merge   X = L^-1 from the inverted diagonal blocks by recursive doubling;
 //  k_xtx         Ainv = X^T X (lower tiles, mirrored).
 // A partial last block is padded with the identity inside the kernels.
 constexpr int kNB = 32;
@@ -562,53 +566,65 @@ __global__ void k_chol_update(double* M, int n, int k0, int k1) {
   }
 }
 
-// Block row bi of X = L^-1 (row-major, lower; the upper part is zero beforehand). CTA j
-// computes X_{bi, j}; CTA bi copies Dinv_bi onto the diagonal. Thread (ty, tx) of the 32 x 8
-// layout owns rows ty, ty + 8, ty + 16, ty + 24 of column tx.
+// X = L^-1 by recursive doubling. The diagonal 32 x 32 blocks of X are the inverted blocks
+// Dinv_k; then, for s = 32, 64, ..., every pair of neighbouring inverted diagonal blocks of
+// size s (rows/columns [p, p + s) and [p + s, p + s + s2), p = 2 s z) is merged into one of
+// size s + s2 by the block formula X21 = -X22 L21 X11, in two tile products per pair:
+//   step 1: T = L21 X11   (X11 lower: output column tile ct needs k >= 32 ct only)
+//   step 2: X21 = -X22 T  (X22 lower: output row tile rt needs k < 32 (rt + 1) only)
+// All pairs of a level run in one launch (blockIdx.z), so every launch fills the GPU with
+// 32 x 32 output tiles; thread (ty, tx) owns rows ty, ty + 8, ty + 16, ty + 24 of column tx.
 __global__ void __launch_bounds__(256)
-k_trinv_row(const double* __restrict__ L, int n, int bi, const double* __restrict__ Dblk,
-            double* __restrict__ X) {
-  __shared__ double As[kNB][kNB + 1], Bs[kNB][kNB + 1];
-  const int bj = blockIdx.x;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int i0 = bi * kNB, j0 = bj * kNB;
-  const double* Di = Dblk + (size_t)bi * kNB * kNB;
-  if (bj == bi) {
-    for (int q = 0; q < 4; ++q) {
-      const int r = ty + 8 * q;
-      if (i0 + r < n && j0 + tx < n) X[(size_t)(i0 + r) * n + j0 + tx] = Di[r * kNB + tx];
-    }
-    return;
+k_inv_diag_blocks(int n, const double* __restrict__ Dblk, double* __restrict__ X) {
+  const int b = blockIdx.x, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double* D = Dblk + (size_t)b * kNB * kNB;
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    if (b * kNB + r < n && b * kNB + tx < n)
+      X[(size_t)(b * kNB + r) * n + b * kNB + tx] = D[r * kNB + tx];
   }
+}
+
+template <int STEP>
+__global__ void __launch_bounds__(256)
+k_inv_merge(const double* __restrict__ L, double* __restrict__ X, double* __restrict__ T, int n,
+            int s) {
+  __shared__ double As[kNB][kNB + 1], Bs[kNB][kNB + 1];
+  const int p = blockIdx.z * 2 * s;
+  const int s2 = min(s, n - p - s);
+  const int rt = blockIdx.y, ct = blockIdx.x;
+  if (s2 <= 0 || rt * kNB >= s2) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int kb = STEP == 1 ? ct * kNB : 0;
+  const int ke = STEP == 1 ? s : min(s2, (rt + 1) * kNB);
+  const double* A = STEP == 1 ? L : X;           // rows p + s + ..., k-columns from a0
+  const double* B = STEP == 1 ? X : T;           // k-rows from a0, columns p + ...
+  const int a0 = STEP == 1 ? p : p + s;
+  const int r0 = p + s + rt * kNB, c0 = p + ct * kNB;
+  const bool col_ok = ct * kNB + tx < s;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int bk = bj; bk < bi; ++bk) {
-    const int k0 = bk * kNB;
+  for (int k0 = kb; k0 < ke; k0 += kNB) {
     __syncthreads();
     for (int q = 0; q < 4; ++q) {
-      const int r = ty + 8 * q;
-      As[r][tx] = (i0 + r < n) ? L[(size_t)(i0 + r) * n + k0 + tx] : 0.0;        // L_{bi, bk}
-      Bs[r][tx] = (j0 + tx < n) ? X[(size_t)(k0 + r) * n + j0 + tx] : 0.0;       // X_{bk, bj}
+      const int rr = ty + 8 * q;
+      As[rr][tx] = (rt * kNB + rr < s2 && k0 + tx < ke)
+                       ? A[(size_t)(r0 + rr) * n + a0 + k0 + tx] : 0.0;
+      Bs[rr][tx] = (k0 + rr < ke && col_ok) ? B[(size_t)(a0 + k0 + rr) * n + c0 + tx] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
     for (int m = 0; m < kNB; ++m) {
-      const double b = Bs[m][tx];
+      const double bv = Bs[m][tx];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][m], b, acc[q]);
+      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][m], bv, acc[q]);
     }
   }
-  __syncthreads();
   for (int q = 0; q < 4; ++q) {
-    const int r = ty + 8 * q;
-    Bs[r][tx] = acc[q];                       // T = sum_k L_ik X_kj
-    As[r][tx] = Di[r * kNB + tx];             // Dinv_i (lower)
-  }
-  __syncthreads();
-  for (int q = 0; q < 4; ++q) {
-    const int r = ty + 8 * q;
-    double s = 0.0;
-    for (int m = 0; m <= r; ++m) s = fma(As[r][m], Bs[m][tx], s);
-    if (i0 + r < n && j0 + tx < n) X[(size_t)(i0 + r) * n + j0 + tx] = -s;
+    const int rr = ty + 8 * q;
+    if (rt * kNB + rr < s2 && col_ok) {
+      const size_t idx = (size_t)(r0 + rr) * n + c0 + tx;
+      if (STEP == 1) T[idx] = acc[q]; else X[idx] = -acc[q];
+    }
   }
 }
 

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("cheb_degree", ctypes.c_int),
                 ("eig_ratio", ctypes.c_double), ("boost", ctypes.c_double),
                 ("power_iters", ctypes.c_int), ("power_seed_base", ctypes.c_int),
-                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("tile_shape", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -86,6 +87,9 @@ def lib():
                                                 ctypes.POINTER(ctypes.c_int)]),
         "rmg_hier_level_export": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "rmg_hier_lambda": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "rmg_hier_tile_shape": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int)]),
         "rmg_hier_coarse_matrix": (ctypes.c_int, [P, I64P, P, P]),
         "rmg_hier_vcycle_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_launch_count": (ctypes.c_ulonglong, []),
@@ -129,7 +133,8 @@ def exported_symbols():
             "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
             "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
-            "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor", "rmg_mlp_num_params", "rmg_mlp_create",
+            "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor",
+            "rmg_hier_tile_shape", "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
             "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
 
@@ -302,6 +307,13 @@ class Hierarchy:
     def level_export(self, level, coeffs=None, dinv=None, gids=None):
         self.ctx.check(lib().rmg_hier_level_export(self.h, level, _ptr(coeffs), _ptr(dinv),
                                                    _ptr(gids)))
+
+    def tile_shape(self, level):
+        """(tx, ty, tz) of the level's stencil-sweep tiles; (0, 0, 0) for runs of 256 nodes."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(lib().rmg_hier_tile_shape(self.h, level, ctypes.byref(a), ctypes.byref(b),
+                                                 ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def lam(self, level):
         v = ctypes.c_double()

@@ -242,3 +242,72 @@ def test_errors_are_reported(ctx):
     assert e.value.status == 2
     # the context is still usable
     lay.operator_from_csr(27, dq.rowptr, dq.col, dq.val)
+
+
+SHAPES = [(0, 0, 0), (32, 8, 1), (64, 4, 1), (128, 2, 1), (16, 16, 1), (32, 4, 2), (16, 8, 2),
+          (16, 4, 4), (8, 8, 4)]
+
+
+@pytest.mark.parametrize("name", ["diff3d_small", "q1_3d_small", "c1_poisson2d"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_shapes_give_identical_cycles(ctx, name, precision):
+    """Every stencil-sweep tile shape (and the autotuned choice) computes each node's row with
+    the same arithmetic, so V-cycles agree bit for bit; 2D levels take only tz = 1 boxes."""
+    from paper_2103_11962_gb300 import rmg, upload
+    p, nlev = _problem(name)
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    ref = None
+    for k in [-1] + list(range(len(SHAPES))):
+        o = rmg.default_options(levels=nlev, precision=precision, tile_shape=k)
+        o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, 1, 1, 3
+        h = rmg.Hierarchy(lay, o)
+        for l in range(nlev - 1):
+            got = h.tile_shape(l)
+            if k >= 0:
+                want = SHAPES[k] if (p.dim == 3 or SHAPES[k][2] == 1) else (0, 0, 0)
+                assert got == want, (k, l, got)
+            else:
+                assert got in SHAPES
+        assert h.tile_shape(nlev - 1) == (0, 0, 0)
+        z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+        h.vcycle(dp.b, z)
+        zc = z.cpu().numpy()
+        if ref is None:
+            ref = zc
+        else:
+            assert np.array_equal(zc, ref), k
+        h.close()
+
+
+def test_tile_shapes_block_operator(ctx):
+    """Box tiles on a 3-dof-per-node (elasticity) hierarchy give the run-tile cycle exactly."""
+    from paper_2103_11962_gb300 import rmg, upload
+    p = W.elasticity3d(region_grid=(2, 2, 2), choices=(10, 19), seed=4)
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_block_csr(27, 3, dp.rowptr, dp.col, dp.val)
+    ref = None
+    for k in (0, 5, 8, -1):
+        o = rmg.default_options(levels=3, smoother=rmg.CHEBYSHEV, nu1=1, nu2=1, cheb_degree=3,
+                                power_iters=30, tile_shape=k)
+        h = rmg.Hierarchy(lay, o)
+        z = torch.empty(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+        h.vcycle(dp.b, z)
+        zc = z.cpu().numpy()
+        if ref is None:
+            ref = zc
+        else:
+            assert np.array_equal(zc, ref), k
+        h.close()
+
+
+def test_bad_tile_shape_is_an_error(ctx):
+    from paper_2103_11962_gb300 import rmg, upload
+    p, nlev = _problem("diff3d_small")
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    with pytest.raises(rmg.RmgError):
+        rmg.Hierarchy(lay, rmg.default_options(levels=nlev, tile_shape=len(SHAPES)))
