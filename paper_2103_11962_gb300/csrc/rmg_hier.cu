@@ -132,21 +132,40 @@ k_cg_update_mixed(int n, int n_nodes, const double* __restrict__ p, const double
 
 // Partial sums of r.z and r.z_old from the FP32 residual copy and the FP32 cycle output, which
 // then becomes z_old. Partials of r.z go to partials[0, gridDim), those of r.z_old to
-// partials[gridDim, 2 gridDim).
+// partials[gridDim, 2 gridDim). Four consecutive entries per thread step (16-byte loads) keep
+// enough bytes in flight; the entries past the last multiple of four take a scalar tail.
+__device__ __forceinline__ void flex_term(float rk, float im, float zk, float zo, float& run0,
+                                          float& run1) {
+  const float r = rk * im;
+  run0 = fmaf(r, zk, run0);
+  run1 = fmaf(r, zo, run1);
+}
+
 __global__ void __launch_bounds__(256)
 k_flex_dots(int n, int n_nodes, const float* __restrict__ r32, const float* __restrict__ z,
             float* __restrict__ zold, const uint8_t* __restrict__ mult,
             double* __restrict__ partials) {
   double s0 = 0.0, s1 = 0.0;
   float run0 = 0.f, run1 = 0.f;
+  const int n4 = n >> 2;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  auto im_of = [&](int k) { return inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]); };
   int cnt = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const float rk = r32[k] * inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]);
-    const float zk = z[k];
-    run0 = fmaf(rk, zk, run0);
-    run1 = fmaf(rk, zold[k], run1);
-    zold[k] = zk;
-    if (++cnt == kRun) { s0 += (double)run0; s1 += (double)run1; run0 = run1 = 0.f; cnt = 0; }
+  for (int q = tid; q < n4; q += nth) {
+    const float4 rv = reinterpret_cast<const float4*>(r32)[q];
+    const float4 zv = reinterpret_cast<const float4*>(z)[q];
+    const float4 ov = reinterpret_cast<const float4*>(zold)[q];
+    const int k = 4 * q;
+    flex_term(rv.x, im_of(k), zv.x, ov.x, run0, run1);
+    flex_term(rv.y, im_of(k + 1), zv.y, ov.y, run0, run1);
+    flex_term(rv.z, im_of(k + 2), zv.z, ov.z, run0, run1);
+    flex_term(rv.w, im_of(k + 3), zv.w, ov.w, run0, run1);
+    reinterpret_cast<float4*>(zold)[q] = zv;
+    if (++cnt == 4) { s0 += (double)run0; s1 += (double)run1; run0 = run1 = 0.f; cnt = 0; }
+  }
+  for (int k = 4 * n4 + tid; k < n; k += nth) {
+    flex_term(r32[k], im_of(k), z[k], zold[k], run0, run1);
+    zold[k] = z[k];
   }
   s0 += (double)run0;
   s1 += (double)run1;
@@ -681,12 +700,42 @@ void opdep_weights(Hier& h, int level, float* wr) {
   RMG_LAUNCHED();
 }
 
+// Composite inner product of two FP32 vectors (the mixed cycle's power method): FP32 products
+// added in runs of 16 before the FP64 accumulation, four entries per thread step.
+__global__ void __launch_bounds__(256)
+k_dot_f32(int n, int n_nodes, const float* __restrict__ x, const float* __restrict__ y,
+          const uint8_t* __restrict__ mult, double* __restrict__ partials) {
+  double s = 0.0;
+  float run = 0.f;
+  const int n4 = n >> 2;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  auto im_of = [&](int k) { return inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]); };
+  int cnt = 0;
+  for (int q = tid; q < n4; q += nth) {
+    const float4 a = reinterpret_cast<const float4*>(x)[q];
+    const float4 b = reinterpret_cast<const float4*>(y)[q];
+    const int k = 4 * q;
+    run = fmaf(a.x * im_of(k), b.x, run);
+    run = fmaf(a.y * im_of(k + 1), b.y, run);
+    run = fmaf(a.z * im_of(k + 2), b.z, run);
+    run = fmaf(a.w * im_of(k + 3), b.w, run);
+    if (++cnt == 4) { s += (double)run; run = 0.f; cnt = 0; }
+  }
+  for (int k = 4 * n4 + tid; k < n; k += nth) run = fmaf(x[k] * im_of(k), y[k], run);
+  s += (double)run;
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // Composite inner product of two consistent regional vectors of any precision (FP64 sums).
 template <typename VT>
 static void dot_t(Ctx& c, int n, int n_nodes, const VT* x, const VT* y, const uint8_t* mult,
                   double* dst, int op, cudaStream_t st) {
   const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
-  k_dot<VT, VT><<<g, 256, 0, st>>>(n, n_nodes, x, y, mult, c.partials.get());
+  if constexpr (sizeof(VT) == 4)
+    k_dot_f32<<<g, 256, 0, st>>>(n, n_nodes, x, y, mult, c.partials.get());
+  else
+    k_dot<VT, VT><<<g, 256, 0, st>>>(n, n_nodes, x, y, mult, c.partials.get());
   RMG_LAUNCHED();
   k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, dst, op);
   RMG_LAUNCHED();

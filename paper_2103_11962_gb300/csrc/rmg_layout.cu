@@ -386,46 +386,80 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
     double zsum = 0.0, offsum = 0.0;
     unsigned seen = 0;                           // slots already filled (27 < 32 bits)
     const int64_t row = (int64_t)g * B + c_row;
-    const int64_t e1 = rowptr[row + 1];
-    for (int64_t e = rowptr[row]; e < e1; ++e) {
-      const int64_t c64 = col[e];
-      const double v = val[e];
-      if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); continue; }
-      int c = (int)c64;
-      if (B > 1) {                                 // compile-time divisor: multiply-shift
-        c = (int)(c64 / B);
-        if ((int)(c64 - (int64_t)c * B) != c_col) continue;
-      }
-      zsum += v;
-      if (c == g) continue;
-      const int sc = copy_in_region(c, R, nodes, c2r, cgrp, gptr, gslot);
-      if (sc < 0) continue;                      // entry belongs to other regions only
-      int dx, dy, dz;
-      if (peel) {
-        box_offset(sc - n, sy, sz, dx, dy, dz);
-      } else {
-        int ic, jc, lc;
-        decode(sc - R.off, R, ic, jc, lc);
-        dx = ic - i; dy = jc - j; dz = lc - l;
-      }
-      const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
-                          j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
-      const int slot = inside ? sten_slot<KIND>(dx, dy, dz) : -1;
-      if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
-      const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
-      const double vs = q == 1 ? v : v * inv_mult<double>(q);
-      offsum += vs;
-      // a CSR row holds one entry per neighbour: place it by selects (integer pipe) and keep
-      // the FP64 accumulation for the rare row with a repeated column
-      const unsigned bit = 1u << slot;
-      if (seen & bit) {
+    const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+    // entries in batches of four: the column, value and group loads of a batch are issued
+    // together (they do not depend on each other), then the entries are applied in order
+    constexpr int U = 4;
+    for (int64_t eb = e0; eb < e1; eb += U) {
+      int64_t cc[U];
+      double vv[U];
 #pragma unroll
-        for (int s = 0; s < S::S; ++s)
-          if (s == slot) acc[s] += vs;
-      } else {
-        seen |= bit;
+      for (int u = 0; u < U; ++u) {
+        cc[u] = eb + u < e1 ? col[eb + u] : -1;
+        vv[u] = eb + u < e1 ? val[eb + u] : 0.0;
+      }
+      int cn[U], grp[U];
 #pragma unroll
-        for (int s = 0; s < S::S; ++s) acc[s] = s == slot ? vs : acc[s];
+      for (int u = 0; u < U; ++u) {
+        cn[u] = -1;
+        grp[u] = -2;
+        if (eb + u >= e1) continue;
+        const int64_t c64 = cc[u];
+        if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); continue; }
+        int c = (int)c64;
+        if (B > 1) {                               // compile-time divisor: multiply-shift
+          c = (int)(c64 / B);
+          if ((int)(c64 - (int64_t)c * B) != c_col) continue;
+        }
+        cn[u] = c;
+        if (c != g) grp[u] = cgrp[c];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = cn[u];
+        if (c < 0) continue;                       // other component, past the row, or error
+        const double v = vv[u];
+        zsum += v;
+        if (c == g) continue;
+        // regional slot of c inside this region (copy_in_region with the group preloaded)
+        int sc = -1;
+        if (grp[u] < 0) {
+          const int s0 = c2r[c];
+          sc = (s0 >= R.off && s0 < R.off + nodes) ? s0 : -1;
+        } else {
+          for (int q = gptr[grp[u]]; q < gptr[grp[u] + 1]; ++q) {
+            const int s0 = gslot[q];
+            if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
+          }
+        }
+        if (sc < 0) continue;                      // entry belongs to other regions only
+        int dx, dy, dz;
+        if (peel) {
+          box_offset(sc - n, sy, sz, dx, dy, dz);
+        } else {
+          int ic, jc, lc;
+          decode(sc - R.off, R, ic, jc, lc);
+          dx = ic - i; dy = jc - j; dz = lc - l;
+        }
+        const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
+                            j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
+        const int slot = inside ? sten_slot<KIND>(dx, dy, dz) : -1;
+        if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
+        const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
+        const double vs = q == 1 ? v : v * inv_mult<double>(q);
+        offsum += vs;
+        // a CSR row holds one entry per neighbour: place it by selects (integer pipe) and
+        // keep the FP64 accumulation for the rare row with a repeated column
+        const unsigned bit = 1u << slot;
+        if (seen & bit) {
+#pragma unroll
+          for (int s = 0; s < S::S; ++s)
+            if (s == slot) acc[s] += vs;
+        } else {
+          seen |= bit;
+#pragma unroll
+          for (int s = 0; s < S::S; ++s) acc[s] = s == slot ? vs : acc[s];
+        }
       }
     }
     acc[S::CENTER] = zsum * inv_mult<double>(mult[n]) - offsum;

@@ -494,8 +494,18 @@ k_chol_diag(double* M, int n, int k0, double* __restrict__ Dblk, int* err) {
       if (ln == 0) set_err(err, DERR_NOT_SPD);
       p = 1.0;
     }
-    const double d = sqrt(p);
-    const double rd = 1.0 / d;
+    // 1/sqrt(p): FP32 seed, then two Newton steps in FP64 (relative error 1e-7 -> 1e-14 ->
+    // rounding), far shorter on the FP64 pipe than a sqrt and a division; pivots outside the
+    // FP32 range take the sqrt and the division
+    double rd;
+    if (p > 1e-30 && p < 1e30) {
+      rd = (double)rsqrtf((float)p);
+      rd = rd * (1.5 - 0.5 * p * rd * rd);
+      rd = rd * (1.5 - 0.5 * p * rd * rd);
+    } else {
+      rd = 1.0 / sqrt(p);
+    }
+    const double d = p * rd;
     __syncwarp();
     if (ln == j) { T[j][j] = d; rdiag[j] = rd; }
     if (ln > j) T[ln][j] *= rd;
