@@ -66,6 +66,17 @@ WORKLOADS = {
     "c5_elasticity_4x4x4": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
                                 power_iters=30,
                                 desc="3D linear elasticity as c5_elasticity on 4x4x4 regions of 28^3"),
+    "c3_q1laplace3d": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                           desc="3D Q1 Laplacian (27-point), 8x8x8 regions of 55^3 nodes (433^3 "
+                                "composite, 81M unknowns, 2.2G nonzeros; CSR assembled on the "
+                                "device by the workload generator), rhs seed 2"),
+    "c5_elasticity_full": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
+                               power_iters=30,
+                               desc="3D linear elasticity, 8x8x8 regions with per-axis node counts "
+                                    "from {28,55} (seed 95, the first seed from 4 on giving "
+                                    "60M +- 15% dofs: 271x271x244 nodes, 53.8M dofs, 4.4G "
+                                    "nonzeros; CSR assembled on the device), E log-normal "
+                                    "(sigma 0.5), nu 0.3, x=0 clamped, uniform body load"),
     "c3_q1laplace3d_slice": dict(levels=4, smoother="chebyshev", nu1=1, nu2=1, degree=3,
                                  desc="3D Q1 Laplacian (27-point), 4x4x4 regions of 55^3 nodes "
                                       "(the 4x4x4-region slice of the 8x8x8 configuration)"),
@@ -105,6 +116,21 @@ def profiled_traffic(prec):
         if key and line.startswith(f"{key}_dram_bytes_per_node:"):
             return float(line.split(":")[1])
     return None
+
+
+def device_problem(p, dev):
+    """Device arrays of a problem: uploaded from the host generator, or already on the device
+    (the workloads assembled there)."""
+    from paper_2103_11962_gb300 import DeviceProblem, upload
+    if hasattr(p, "rowptr"):
+        import numpy as np
+        import torch
+        return DeviceProblem(dim=p.dim, stencil=p.stencil, n=p.n_nodes,
+                             region_dims=np.asarray(p.region_dims, dtype=np.int32),
+                             rowptr=p.rowptr, col=p.col, val=p.val, b=p.b,
+                             gids=torch.from_numpy(p.region_gids).to(dev),
+                             dirichlet=torch.from_numpy(p.dirichlet).to(dev))
+    return upload(p, dev)
 
 
 def max_over_ranks(ms, dist, device):
@@ -286,9 +312,15 @@ def main():
         p = W.elasticity3d(region_grid=(4, 4, 4), choices=(28,), seed=4)
     elif args.workload == "c3_q1laplace3d_slice":
         p = W.q1_laplace3d(region_grid=(4, 4, 4), n=55, seed=2)
+    elif args.workload == "c3_q1laplace3d":
+        from workloads import device as WD
+        p = WD.q1_laplace3d(region_grid=(8, 8, 8), n=55, seed=2, device=dev)
+    elif args.workload == "c5_elasticity_full":
+        from workloads import device as WD
+        p = WD.elasticity3d(region_grid=(8, 8, 8), choices=(28, 55), seed=95, device=dev)
     else:
         p = W.config(args.workload)
-    dp = upload(p, dev)
+    dp = device_problem(p, dev)
     stream = torch.cuda.current_stream(local_rank)
     ctx = rmg.Context(local_rank, stream.cuda_stream)
     t_lay = time.perf_counter()
@@ -425,7 +457,8 @@ def main():
         "config": {"workload": args.workload, "desc": cfg["desc"],
                    "global_dims": list(p.global_dims), "regions": int(p.nregions),
                    "unknowns": p.n_unknowns, "regional_nodes": p.n_regional_nodes,
-                   "composite_nnz": int(p.A.nnz), "levels": cfg["levels"],
+                   "composite_nnz": int(p.nnz if hasattr(p, "nnz") else p.A.nnz),
+                   "levels": cfg["levels"],
                    "precision": prec, "rtol": RTOL,
                    "dofs_per_node": p.dofs_per_node,
                    "l2": "inputs larger than L2 (no flush needed)"
@@ -516,7 +549,11 @@ def main():
     # end to end through the C ABI with host buffers: H2D of the step's inputs (composite
     # CSR + right-hand side) from pinned memory, the step, D2H of the solution
     if not args.no_e2e:
-        hp = {k: getattr(dp, k).cpu().pin_memory() for k in ("rowptr", "col", "val", "b")}
+        hp = {}
+        for k in ("rowptr", "col", "val", "b"):
+            t = getattr(dp, k)
+            hp[k] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            hp[k].copy_(t)
         hx = torch.empty(p.n, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in hp.values())
         d2h = hx.numel() * hx.element_size()

@@ -296,24 +296,6 @@ void layout_create(Ctx& c, Level& L, int dim, int nreg, const int* dims, const i
 
 // ------------------------------------------------------------------ splitting (Sec. 4)
 namespace {
-// Regional slot of composite node cg inside region k, or -1.
-__device__ __forceinline__ int copy_in_region(int cg, const RegionDev& R, int nodes,
-                                              const int* __restrict__ c2r,
-                                              const int* __restrict__ cgrp,
-                                              const int* __restrict__ gptr,
-                                              const int* __restrict__ gslot) {
-  const int grp = cgrp[cg];
-  if (grp < 0) {
-    const int s = c2r[cg];
-    return (s >= R.off && s < R.off + nodes) ? s : -1;
-  }
-  for (int q = gptr[grp]; q < gptr[grp + 1]; ++q) {
-    const int s = gslot[q];
-    if (s >= R.off && s < R.off + nodes) return s;
-  }
-  return -1;
-}
-
 // Number of regions holding both composite nodes a and b. Group slots are ascending and
 // regions occupy ascending slot ranges, so the region ids of a group are ascending too and the
 // regions common to the two groups are found by one merge of the two lists.
@@ -361,6 +343,12 @@ __device__ __forceinline__ void box_offset(int d, int sy, int sz, int& dx, int& 
   dx = d;
 }
 
+// One regional node per thread and one row component c per blockIdx.y: the thread scans the
+// CSR row g * B + c once and writes every entry straight into its coefficient stream
+// coef[((c * B + c') * S + slot) * n_r + n] (threads of a warp are consecutive nodes, so for
+// interior rows the stores of one entry index are contiguous). A slot that receives no entry
+// is zeroed at the end; the diagonal slot takes the nullspace rule; a repeated column (not
+// produced by a well-formed CSR) is accumulated.
 template <int KIND, int B>
 __global__ void __launch_bounds__(kTile)
 k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
@@ -370,8 +358,7 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
             const int64_t* __restrict__ col, const double* __restrict__ val, int ncomp,
             double* __restrict__ coef, int* err) {
   using S = Sten<KIND>;
-  // block (c, cp) of a B-dof operator: rows g*B + c, columns g'*B + cp (blockIdx.y = c*B + cp)
-  const int c_row = blockIdx.y / B, c_col = blockIdx.y % B;
+  const int c_row = blockIdx.y;
   RMG_FOR_NODES(G)
     int i, j, l;
     decode(li, R, i, j, l);
@@ -380,11 +367,11 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
     const bool peel = R.nx >= 3 && R.ny >= 3;    // box_offset is exact
     const int g = gid[n];
     const bool shared = mult[n] > 1;
-    double acc[S::S];
+    double zsum[B], offsum[B];
+    unsigned seen[B];                            // slots already written (27 < 32 bits)
 #pragma unroll
-    for (int s = 0; s < S::S; ++s) acc[s] = 0.0;
-    double zsum = 0.0, offsum = 0.0;
-    unsigned seen = 0;                           // slots already filled (27 < 32 bits)
+    for (int b = 0; b < B; ++b) { zsum[b] = 0.0; offsum[b] = 0.0; seen[b] = 0u; }
+    double* cbase = coef + (size_t)c_row * B * S::S * G.n_r + n;
     const int64_t row = (int64_t)g * B + c_row;
     const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
     // entries in batches of four: the column, value and group loads of a batch are issued
@@ -398,10 +385,11 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
         cc[u] = eb + u < e1 ? col[eb + u] : -1;
         vv[u] = eb + u < e1 ? val[eb + u] : 0.0;
       }
-      int cn[U], grp[U];
+      int cn[U], cp[U], grp[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         cn[u] = -1;
+        cp[u] = 0;
         grp[u] = -2;
         if (eb + u >= e1) continue;
         const int64_t c64 = cc[u];
@@ -409,7 +397,7 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
         int c = (int)c64;
         if (B > 1) {                               // compile-time divisor: multiply-shift
           c = (int)(c64 / B);
-          if ((int)(c64 - (int64_t)c * B) != c_col) continue;
+          cp[u] = (int)(c64 - (int64_t)c * B);
         }
         cn[u] = c;
         if (c != g) grp[u] = cgrp[c];
@@ -417,11 +405,12 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int c = cn[u];
-        if (c < 0) continue;                       // other component, past the row, or error
+        if (c < 0) continue;                       // past the row, or an error
+        const int b = cp[u];
         const double v = vv[u];
-        zsum += v;
+        zsum[b] += v;
         if (c == g) continue;
-        // regional slot of c inside this region (copy_in_region with the group preloaded)
+        // regional slot of c inside this region (its group was loaded above)
         int sc = -1;
         if (grp[u] < 0) {
           const int s0 = c2r[c];
@@ -447,25 +436,25 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
         if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
         const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
         const double vs = q == 1 ? v : v * inv_mult<double>(q);
-        offsum += vs;
-        // a CSR row holds one entry per neighbour: place it by selects (integer pipe) and
-        // keep the FP64 accumulation for the rare row with a repeated column
+        offsum[b] += vs;
+        double* dst = cbase + ((size_t)b * S::S + slot) * G.n_r;
         const unsigned bit = 1u << slot;
-        if (seen & bit) {
-#pragma unroll
-          for (int s = 0; s < S::S; ++s)
-            if (s == slot) acc[s] += vs;
+        if (seen[b] & bit) {
+          *dst += vs;
         } else {
-          seen |= bit;
-#pragma unroll
-          for (int s = 0; s < S::S; ++s) acc[s] = s == slot ? vs : acc[s];
+          seen[b] |= bit;
+          *dst = vs;
         }
       }
     }
-    acc[S::CENTER] = zsum * inv_mult<double>(mult[n]) - offsum;
-    double* cb = coef + (size_t)blockIdx.y * S::S * G.n_r;
 #pragma unroll
-    for (int s = 0; s < S::S; ++s) cb[(size_t)s * G.n_r + n] = acc[s];
+    for (int b = 0; b < B; ++b) {
+      double* cb = cbase + (size_t)b * S::S * G.n_r;
+#pragma unroll
+      for (int s = 0; s < S::S; ++s)
+        if (s != S::CENTER && !((seen[b] >> s) & 1u)) cb[(size_t)s * G.n_r] = 0.0;
+      cb[(size_t)S::CENTER * G.n_r] = zsum[b] * inv_mult<double>(mult[n]) - offsum[b];
+    }
   RMG_END_FOR_NODES
 }
 
@@ -513,7 +502,7 @@ void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, co
     k_region_ids<<<persistent_grid(c, G.ntiles), kTile, 0, c.stream>>>(G, L.rid.get());
     RMG_LAUNCHED();
   }
-  const dim3 gb(persistent_grid(c, G.ntiles), B * B);
+  const dim3 gb(persistent_grid(c, G.ntiles), B);
 #define RMG_SPLIT(K, BB)                                                                    \
   k_split_csr<K, BB><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(), \
                                                  L.cgrp.get(), L.gptr.get(), L.gslot.get(),  \
