@@ -29,7 +29,7 @@ from .rng import uniform_pm1
 
 @dataclass
 class Options:
-    smoother: str = "jacobi"     # "jacobi" or "chebyshev"
+    smoother: str = "jacobi"     # "jacobi", "chebyshev" or "gs" (region Gauss-Seidel)
     nu1: int = 2                 # pre-smoothing: Jacobi sweeps / Chebyshev applications
     nu2: int = 2                 # post-smoothing
     omega: float = 0.67
@@ -61,6 +61,32 @@ def power_start(level: Level, l: int, opts: Options):
     x = uniform_pm1(opts.power_seed_base + l, level.layout.counter_ids())
     x[level.layout.mask] = 0.0
     return x
+
+
+def gs_colours(level: Level):
+    """Colour of every regional node for the multicolour region Gauss-Seidel: the parity of
+    i + j + l (2 colours) when the level's operator couples only nodes that differ along one
+    axis (5- and 7-point stencils), else the parities of i, j and l (4 colours in 2D, 8 in 3D:
+    9- and 27-point stencils). Nodes of one colour are never coupled."""
+    lay = level.layout
+    i_all, j_all, l_all = [], [], []
+    for (nx, ny, nz) in np.asarray(lay.region_dims):
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        i_all.append(x.ravel()); j_all.append(y.ravel()); l_all.append(z.ravel())
+    i, j, l = np.concatenate(i_all), np.concatenate(j_all), np.concatenate(l_all)
+    Ar = level.Ar.tocoo()
+    B = level.Ar.shape[0] // i.shape[0]
+    rr, cc = Ar.row % i.shape[0], Ar.col % i.shape[0]
+    axes = ((i[rr] != i[cc]).astype(int) + (j[rr] != j[cc]).astype(int) +
+            (l[rr] != l[cc]).astype(int))
+    dim3 = bool(np.any(np.asarray(lay.region_dims)[:, 2] > 1))
+    if not np.any(axes > 1):
+        col = (i + j + l) & 1
+        ncol = 2
+    else:
+        col = (i & 1) | ((j & 1) << 1) | ((l & 1) << 2)
+        ncol = 8 if dim3 else 4
+    return np.tile(col, B), ncol
 
 
 class CompositeMG:
@@ -118,11 +144,16 @@ class RegionalMG:
         lev = self.levels[l]
         return b - lev.layout.interface_sum(lev.Ar @ u)
 
-    def smooth(self, l, u, b, nu):
+    def smooth(self, l, u, b, nu, post=False):
         lev, o = self.levels[l], self.opts
         res = lambda uu, bb: self.residual(l, uu, bb)
         if o.smoother == "jacobi":
             return smoothers.jacobi(u, b, res, lev.Dinv_r, o.omega, nu)
+        if o.smoother == "gs":
+            colours, ncol = gs_colours(lev)
+            order = list(range(ncol))[::-1] if post else list(range(ncol))
+            return smoothers.gauss_seidel_colored(u, b, res, lambda d: lev.Ar @ d, lev.Dinv_r,
+                                                  o.omega, nu, colours, order)
         a, bt = smoothers.chebyshev_bounds(lev.lam_r, o.eig_ratio, o.boost)
         for _ in range(nu):
             u = smoothers.chebyshev(u, b, res, lev.Dinv_r, a, bt, o.degree)
@@ -148,7 +179,7 @@ class RegionalMG:
         w = self.restrict(l, r)
         ubar = self.cycle(np.zeros(lev.Pr.shape[1]), w, l + 1)
         u = u + lev.Pr @ ubar
-        return self.smooth(l, u, b, self.opts.nu2)
+        return self.smooth(l, u, b, self.opts.nu2, post=True)
 
     def precondition(self, r):
         return self.cycle(np.zeros_like(r), r)

@@ -10,7 +10,9 @@ from __future__ import annotations
 import numpy as np
 
 
-def pcg(A, b, precond, rtol=1e-10, maxit=200, x0=None):
+def pcg(A, b, precond, rtol=1e-10, maxit=200, x0=None, flexible=False):
+    """Preconditioned CG; flexible=True takes the Polak-Ribiere form
+    beta = r.(z - z_old) / r_old.z_old for a preconditioner that is not exactly symmetric."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - A @ x
     bnorm = np.linalg.norm(b)
@@ -29,9 +31,10 @@ def pcg(A, b, precond, rtol=1e-10, maxit=200, x0=None):
         hist.append(np.linalg.norm(r) / bnorm)
         if hist[-1] <= rtol:
             break
+        z_old = z
         z = precond(r)
         rz_new = float(r @ z)
-        beta = rz_new / rz
+        beta = (rz_new - float(r @ z_old)) / rz if flexible else rz_new / rz
         rz = rz_new
         p = z + beta * p
     return x, it, hist

@@ -23,6 +23,28 @@ def jacobi(u, b, residual, dinv, omega, sweeps):
     return u
 
 
+def gauss_seidel_colored(u, b, residual, local_apply, dinv, omega, sweeps, colours, order):
+    """Region Gauss-Seidel of Algorithm 1 with the nodes of every region visited colour by
+    colour (``colours`` gives each regional node its colour, ``order`` the colour sequence).
+
+    Each sweep recomputes the regional residual r (with the interface sum), sets delta = 0,
+    and then for every colour class: r_i <- r_i - sum_j A^(l)_ij delta_j with the region's
+    own matrix (``local_apply`` = [[A]] delta, no interface sum), delta_i = omega r_i / d~_ii,
+    u_i <- u_i + delta_i. Copies of an interface node are updated by their own regions and
+    need not agree afterwards (as the paper notes for Algorithm 1).
+    """
+    u = u.copy()
+    for _ in range(sweeps):
+        r = residual(u, b)
+        delta = np.zeros_like(u)
+        for c in order:
+            sel = colours == c
+            rc = r[sel] - local_apply(delta)[sel]
+            delta[sel] = omega * rc * dinv[sel]
+            u[sel] = u[sel] + delta[sel]
+    return u
+
+
 def chebyshev_bounds(lam_max_est, eig_ratio=20.0, boost=1.1):
     """[alpha, beta] = [lambda~/eta, boost * lambda~] (Sec. 3.4, Ifpack2 convention)."""
     return lam_max_est / eig_ratio, boost * lam_max_est

@@ -684,3 +684,53 @@ def test_piecewise_constant_galerkin_closed_form():
     st = {(j % cNx - x, j // cNx - y): v for j, v in zip(row.indices, row.data) if v != 0}
     assert st == pytest.approx({(0, 0): 12.0, (1, 0): -3.0, (-1, 0): -3.0, (0, 1): -3.0,
                                 (0, -1): -3.0})
+
+
+# ------------------------------------------------------------- region Gauss-Seidel (Algorithm 1)
+@pytest.mark.parametrize("make", [
+    lambda: W.poisson2d_5pt(region_grid=(1, 1), n=19, seed=3),
+    lambda: W.diffusion3d_7pt(region_grid=(1, 1, 1), choices=(10,), seed=3),
+    lambda: W.q1_laplace3d(region_grid=(1, 1, 1), n=10, seed=3),
+])
+@pytest.mark.parametrize("omega", [1.0, 0.8])
+def test_gauss_seidel_sweep_is_the_triangular_solve(make, omega):
+    """On a single region, one sweep of the multicolour region Gauss-Seidel is the textbook
+    SOR step u + (D/omega + L)^-1 (b - A u), with L the strictly lower part of A in the colour
+    order (nodes of one colour are uncoupled, so their order inside a colour is free)."""
+    import scipy.sparse.linalg as spla
+    from oracle import cycle, hierarchy, smoothers
+    p = make()
+    lev = hierarchy.build(p, 1)[0]
+    A = lev.Ar.tocsr()
+    colours, ncol = cycle.gs_colours(lev)
+    rng = np.random.default_rng(5)
+    u0 = rng.standard_normal(A.shape[0])
+    b = rng.standard_normal(A.shape[0])
+    got = smoothers.gauss_seidel_colored(u0, b, lambda u, bb: bb - A @ u, lambda d: A @ d,
+                                         lev.Dinv_r, omega, 1, colours, list(range(ncol)))
+    perm = np.argsort(colours, kind="stable")
+    Ap = A[perm][:, perm].tocsr()
+    M = (sp.tril(Ap, k=-1) + sp.diags(Ap.diagonal() / omega)).tocsr()
+    r = (b - A @ u0)[perm]
+    delta = spla.spsolve_triangular(M, r, lower=True)
+    expect = u0.copy()
+    expect[perm] += delta
+    assert np.abs(got - expect).max() <= 1e-12 * np.abs(expect).max()
+    # the colouring leaves no coupling inside a colour
+    C = A.tocoo()
+    off = C.row != C.col
+    assert not np.any(colours[C.row[off]] == colours[C.col[off]])
+
+
+def test_flexible_pcg_equals_pcg_for_a_symmetric_preconditioner():
+    """With a symmetric fixed preconditioner r.z_old vanishes in exact arithmetic, so the
+    flexible (Polak-Ribiere) beta gives the same iterates as the classical one."""
+    from oracle import cycle, hierarchy, krylov
+    p = W.diffusion3d_7pt(region_grid=(2, 2, 1), choices=(10, 19), seed=8)
+    mg = cycle.RegionalMG(hierarchy.build(p, 2), cycle.Options(smoother="jacobi", nu1=2, nu2=2,
+                                                               omega=0.67))
+    pre = krylov.regional_preconditioner(mg)
+    x1, it1, h1 = krylov.pcg(p.A, p.b, pre, rtol=1e-10)
+    x2, it2, h2 = krylov.pcg(p.A, p.b, pre, rtol=1e-10, flexible=True)
+    assert it1 == it2
+    assert np.allclose(h1, h2, rtol=1e-6, atol=0)
