@@ -270,6 +270,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2_diffusion3d", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--smoother", default=None, choices=["jacobi", "chebyshev", "gs"],
+                    help="override the workload's smoother (gs: region Gauss-Seidel, "
+                         "Algorithm 1, nu 1/1, omega 1)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -331,10 +334,15 @@ def main():
         o = rmg.default_options(levels=cfg["levels"], precision={"fp64": rmg.FP64,
                                                                 "fp32": rmg.FP32,
                                                                 "bf16": rmg.FP32_BF16COEF}[prec])
-        if cfg["smoother"] == "chebyshev":
-            o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, cfg["nu1"], cfg["nu2"], cfg["degree"]
+        sm = args.smoother or cfg["smoother"]
+        if sm == "chebyshev":
+            o.smoother, o.nu1, o.nu2, o.cheb_degree = (rmg.CHEBYSHEV, cfg["nu1"], cfg["nu2"],
+                                                        cfg.get("degree", 3))
+        elif sm == "gs":
+            o.smoother, o.nu1, o.nu2, o.omega = rmg.GAUSS_SEIDEL, 1, 1, 1.0
         else:
-            o.smoother, o.nu1, o.nu2, o.omega = rmg.JACOBI, cfg["nu1"], cfg["nu2"], cfg["omega"]
+            o.smoother, o.nu1, o.nu2, o.omega = (rmg.JACOBI, cfg["nu1"], cfg["nu2"],
+                                                 cfg.get("omega", 0.67))
         o.power_iters = cfg.get("power_iters", 10)
         return o
 
@@ -455,6 +463,7 @@ def main():
         "dtype": {"fp64": "f64", "fp32": "f32 cycle + f64 CG", "bf16": "f32/bf16 cycle + f64 CG"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": cfg["desc"],
+                   "smoother": args.smoother or cfg["smoother"],
                    "global_dims": list(p.global_dims), "regions": int(p.nregions),
                    "unknowns": p.n_unknowns, "regional_nodes": p.n_regional_nodes,
                    "composite_nnz": int(p.nnz if hasattr(p, "nnz") else p.A.nnz),

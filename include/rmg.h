@@ -53,7 +53,19 @@ typedef enum {
   RMG_ERR_STATE = 8          /* call out of order (e.g. setup before an operator is set)   */
 } rmg_status;
 
-typedef enum { RMG_SMOOTHER_JACOBI = 0, RMG_SMOOTHER_CHEBYSHEV = 1 } rmg_smoother;
+/* Smoothers (Sec. 3.4): damped Jacobi, Chebyshev (Algorithm 2), and the region Gauss-Seidel of
+ * Algorithm 1 in multicolour order: every sweep recomputes the regional residual (with the
+ * interface sum) and then visits the colour classes of every region (2 colours for 5/7-point
+ * stencils, the parities of i, j, l for 9/27-point ones; ascending colours before the coarse
+ * correction, descending after it), each node taking delta = omega r / d~ from its residual
+ * corrected by the region's own already-updated neighbours. Copies of interface nodes are
+ * updated by their own regions and need not agree (as the paper notes); rmg_pcg_solve uses
+ * the flexible CG form with it. Scalar operators only (RMG_ERR_ARG for B > 1). */
+typedef enum {
+  RMG_SMOOTHER_JACOBI = 0,
+  RMG_SMOOTHER_CHEBYSHEV = 1,
+  RMG_SMOOTHER_GS = 2
+} rmg_smoother;
 
 /* Arithmetic of the V-cycle. The outer CG always runs in FP64. */
 typedef enum {

@@ -240,10 +240,46 @@ struct Exec {
     flip(l);
   }
 
-  void smooth(int l, int nu, bool from_zero, bool probe_it = false) {
+  // One colour class of the region Gauss-Seidel on level l.
+  void gs_colour(int l, int colour, VT omega) {
+    const Level& L = *h.lv[l];
+    const Grid G = h.sweep(l) ? *h.sweep(l) : L.grid();
+    const int gb = persistent_grid(c(), G.ntiles);
+    VT* u = cur[l];
+#define RMG_GS(K)                                                                             \
+  k_gs_colour<K, CT, VT><<<gb, kTile, 0, st>>>(G, coef(l), V(l).r.get(), dinv(l),               \
+                                               V(l).d.get(), u, colour, omega)
+    switch (L.kind) {
+      case 5: RMG_GS(5); break;
+      case 7: RMG_GS(7); break;
+      case 9: RMG_GS(9); break;
+      default: RMG_GS(27); break;
+    }
+#undef RMG_GS
+    RMG_LAUNCHED();
+    ++launches;
+  }
+
+  void smooth(int l, int nu, bool from_zero, bool probe_it = false, bool post = false) {
     const Level& L = *h.lv[l];
     const int n = L.B * L.n_r;
     const VT omega = VT(h.o.omega);
+    if (h.o.smoother == RMG_SMOOTHER_GS) {
+      const int ncol = (L.kind == 5 || L.kind == 7) ? 2 : (L.dim == 3 ? 8 : 4);
+      for (int s = 0; s < nu; ++s) {
+        if (s == 0 && from_zero) {
+          k_gs_zero<VT><<<elementwise_grid(n), 256, 0, st>>>(n, V(l).b.get(), V(l).r.get(),
+                                                             V(l).d.get(), cur[l]);
+          RMG_LAUNCHED();
+          ++launches;
+        } else {
+          probe = probe_it && s == 0;
+          stencil(l, cur[l], EpiResidZero<VT>{V(l).b.get(), V(l).r.get(), V(l).d.get()});
+        }
+        for (int k = 0; k < ncol; ++k) gs_colour(l, post ? ncol - 1 - k : k, omega);
+      }
+      return;
+    }
     if (h.o.smoother == RMG_SMOOTHER_JACOBI) {
       for (int s = 0; s < nu; ++s) {
         if (s == 0 && from_zero) {
@@ -377,6 +413,7 @@ struct Exec {
   }
 
   int level0_flips() const {
+    if (h.o.smoother == RMG_SMOOTHER_GS) return 0;       // Gauss-Seidel updates u in place
     const int per = (h.o.smoother == RMG_SMOOTHER_JACOBI) ? 1 : h.o.cheb_degree;
     return (h.o.nu1 + h.o.nu2) * per;
   }
@@ -395,8 +432,22 @@ struct Exec {
     coarse(Lv - 1);
     for (int l = Lv - 2; l >= 0; --l) {
       prolong(l);
-      smooth(l, h.o.nu2, false, l == 0);
+      smooth(l, h.o.nu2, false, l == 0, true);
     }
+    if (h.o.smoother == RMG_SMOOTHER_GS && Lv > 1) consistent_output();
+  }
+
+  // The cycle's output as a consistent regional vector: the copies of an interface node take
+  // their mean, the composite value (Psi Psi^T)^-1 Psi u of the preconditioner's output.
+  void consistent_output() {
+    const Level& L = *h.lv[0];
+    if (!L.ngroups) return;
+    launch_groups(c(), L, (const VT*)cur[0], EpiMean<VT>{V(0).y.get()}, st);
+    ++launches;
+    k_copy_slots<VT><<<persistent_grid(c(), (L.nslots + 255) / 256), 256, 0, st>>>(
+        L.nslots, L.gslot.get(), V(0).y.get(), cur[0]);
+    RMG_LAUNCHED();
+    ++launches;
   }
 };
 
@@ -485,7 +536,8 @@ void hier_build(Hier& h) {
   const rmg_options& o = h.o;
   RMG_REQUIRE(o.levels >= 1 && o.levels <= 16, RMG_ERR_ARG, "levels must be in [1, 16]");
   RMG_REQUIRE(o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 0, RMG_ERR_ARG, "bad nu1/nu2");
-  RMG_REQUIRE(o.smoother == RMG_SMOOTHER_JACOBI || o.smoother == RMG_SMOOTHER_CHEBYSHEV,
+  RMG_REQUIRE(o.smoother == RMG_SMOOTHER_JACOBI || o.smoother == RMG_SMOOTHER_CHEBYSHEV ||
+                  o.smoother == RMG_SMOOTHER_GS,
               RMG_ERR_ARG, "unknown smoother");
   RMG_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, RMG_ERR_ARG, "cheb_degree in [1, 8]");
   RMG_REQUIRE(o.precision >= 0 && o.precision <= 2, RMG_ERR_ARG, "unknown precision");
@@ -493,6 +545,8 @@ void hier_build(Hier& h) {
               "tile_shape must be -1 (autotune) or a shape index");
   RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1 &&
               o.power_iters <= 100, RMG_ERR_ARG, "bad Chebyshev options");
+  RMG_REQUIRE(o.smoother != RMG_SMOOTHER_GS || h.layout->L0.B == 1, RMG_ERR_ARG,
+              "the region Gauss-Seidel smoother is for scalar operators");
   h.lv.push_back(&h.layout->L0);
   for (int l = 1; l < o.levels; ++l) {
     h.own.emplace_back(new Level());
@@ -1136,6 +1190,9 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   const int dg = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
   Scalars* sc = h.sc.get();
   const bool mixed = h.mixed();
+  // the Gauss-Seidel cycle is not exactly symmetric (interface copies drift apart within a
+  // sweep): flexible CG for it in FP64 too
+  const bool flex64 = !mixed && h.o.smoother == RMG_SMOOTHER_GS;
   double* rvec = h.v64[0].b.get();     // the V-cycle reads its right-hand side here
   double* zvec = h.v64[0].u.get();     // and leaves its result here (FP64 cycle)
   double* breg = h.tmp.get();
@@ -1189,6 +1246,10 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
       k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.p.get());
       RMG_LAUNCHED();
+      if (flex64) {
+        k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+        RMG_LAUNCHED();
+      }
     }
     for (it = 1; it <= maxit; ++it) {
       launch_stencil(c, L0, L0.coef.get(), h.p.get(), h.v64[0].y.get(),
@@ -1225,7 +1286,12 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
         RMG_LAUNCHED();
       } else {
         dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
-        k_beta<<<1, 1, 0, st>>>(sc, 0);
+        if (flex64) {
+          dot(c, n, L0.n_r, rvec, h.zold.get(), L0.mult.get(), &sc->beta, FIN_STORE, st);
+          k_copy<double><<<eg, 256, 0, st>>>(n, zvec, h.zold.get());
+          RMG_LAUNCHED();
+        }
+        k_beta<<<1, 1, 0, st>>>(sc, flex64 ? 1 : 0);
         RMG_LAUNCHED();
         k_p_update<double><<<eg, 256, 0, st>>>(n, zvec, sc, h.p.get());
         RMG_LAUNCHED();

@@ -290,6 +290,73 @@ __global__ void k_cheb0_zero(int n, const T* __restrict__ b, const T* __restrict
   }
 }
 
+// ------------------------------------------------------------------ region Gauss-Seidel
+// Algorithm 1 in multicolour order. A sweep starts with r = b - Psi^T Psi [[A]] u at every copy
+// (the stencil pair with EpiResidZero, which also sets delta = 0), then runs one launch per
+// colour class.
+template <typename T>
+struct EpiResidZero {              // r = b - A u, delta = 0
+  const T* b; T* r; T* delta;
+  __device__ void operator()(int n, T au, int) const {
+    r[n] = b[n] - au;
+    delta[n] = T(0);
+  }
+};
+
+// The composite value (mean over the copies) of an interface node, written to `out` at every
+// copy: the last step of a Gauss-Seidel cycle, whose copies drift apart within a sweep.
+template <typename T>
+struct EpiMean {
+  T* out;
+  __device__ void operator()(int n, T s, int m) const { out[n] = s * inv_mult<T>(m); }
+};
+
+// dst[gslot[q]] = src[gslot[q]] for every copy of every interface node.
+template <typename T>
+__global__ void k_copy_slots(int nslots, const int* __restrict__ gslot, const T* __restrict__ src,
+                             T* __restrict__ dst) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += gridDim.x * blockDim.x)
+    dst[gslot[q]] = src[gslot[q]];
+}
+
+// A sweep from u = 0: r = b, delta = 0, u = 0.
+template <typename VT>
+__global__ void k_gs_zero(int n, const VT* __restrict__ b, VT* __restrict__ r,
+                          VT* __restrict__ delta, VT* __restrict__ u) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    r[k] = b[k];
+    delta[k] = VT(0);
+    u[k] = VT(0);
+  }
+}
+
+// Colour of a regional node: parity of i + j + l for 5/7-point stencils (2 colours), the
+// parities of i, j, l for 9/27-point ones (4 colours in 2D, 8 in 3D). Nodes of one colour are
+// never coupled by the stencil.
+template <int KIND>
+__device__ __forceinline__ int gs_colour_of(int i, int j, int l) {
+  return (KIND == 5 || KIND == 7) ? ((i + j + l) & 1) : ((i & 1) | ((j & 1) << 1) | ((l & 1) << 2));
+}
+
+// One colour class of the region Gauss-Seidel: at the nodes of colour `colour` of every
+// region, delta_i = omega (r_i - sum_j A^(k)_ij delta_j) / d~_ii with the region's own stencil
+// (no interface sum; delta is zero at the nodes not yet visited in this sweep, the node itself
+// included) and u_i += delta_i.
+template <int KIND, typename CT, typename VT>
+__global__ void __launch_bounds__(kTile)
+k_gs_colour(Grid G, const CT* __restrict__ coef, const VT* __restrict__ r,
+            const VT* __restrict__ dinv, VT* delta, VT* __restrict__ u, int colour, VT omega) {
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    RMG_DECODE(i, j, l);
+    if (gs_colour_of<KIND>(i, j, l) != colour) continue;
+    const VT au = stencil_row<KIND, CT, VT, VT>(coef, delta, n, G.n_r, i, j, l, R);
+    const VT d = omega * (r[n] - au) * dinv[n];
+    delta[n] = d;
+    u[n] = u[n] + d;
+  RMG_END_FOR_NODES
+}
+
 // ------------------------------------------------------------------ transfers (Sec. 3.3)
 // 1D linear 3:1 interpolation: a fine node with remainder rem = i mod 3 takes weight
 // 1 - rem/3 from coarse node i/3 and rem/3 from coarse node i/3 + 1. Seen from a coarse node,

@@ -21,7 +21,7 @@ RMG_OK = 0
 STATUS = {0: "RMG_OK", 1: "RMG_ERR_ARG", 2: "RMG_ERR_LAYOUT", 3: "RMG_ERR_CUDA",
           4: "RMG_ERR_NOMEM", 5: "RMG_ERR_SINGULAR", 6: "RMG_ERR_NOT_CONVERGED",
           7: "RMG_ERR_TIMEOUT", 8: "RMG_ERR_STATE"}
-JACOBI, CHEBYSHEV = 0, 1
+JACOBI, CHEBYSHEV, GAUSS_SEIDEL = 0, 1, 2
 FP64, FP32, FP32_BF16COEF = 0, 1, 2
 
 
