@@ -279,6 +279,10 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-operators", type=int, default=40)
     ap.add_argument("--json-out", default=None, help="also write the JSON line to this file")
+    ap.add_argument("--rap-table", action="store_true",
+                    help="time the Galerkin triple product alone on the single-region 2D "
+                         "9-point meshes of the paper's Table 4 (constant, linear and generic "
+                         "stored transfers) and print that table as the JSON line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -290,6 +294,10 @@ def main():
         if rank != 0:
             return
         reference_arm(args, cfg)
+        return
+    if args.rap_table:
+        if rank == 0:
+            rap_table(args)
         return
 
     import numpy as np
@@ -596,6 +604,84 @@ def main():
                 f.write(json.dumps(out) + "\n")
     if dist:
         dist.destroy_process_group()
+
+
+# The paper's Table 4 (serial CPU seconds, Trilinos/MueLu vs its structured kernels), as context.
+PAPER_TABLE4 = {(140, 36): dict(muelu_9pt=.0024, const=.0001, muelu_25pt=.0109, generic=.0012,
+                                geo=.0009),
+                (140, 180): dict(muelu_9pt=.0124, const=.0006, muelu_25pt=.0572, generic=.0061,
+                                 geo=.0046),
+                (700, 180): dict(muelu_9pt=.0726, const=.0070, muelu_25pt=.2944, generic=.0320,
+                                 geo=.0240),
+                (700, 900): dict(muelu_9pt=.3702, const=.0356, muelu_25pt=1.4786,
+                                 generic=.1606, geo=.1208)}
+
+
+def rap_table(args):
+    """Galerkin triple product [[R]][[A]][[P]] alone (rmg_hier_galerkin, FP64, CUDA events) on
+    one region of (3 nx - 2) x (3 ny - 2) nodes with the 2D Q1 9-point operator, for the coarse
+    meshes of Table 4: piecewise-constant (Const), linear (Geo, implicit weights) and generic
+    stored per-node weights (Generic)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2103_11962_gb300 import rmg, upload
+    dev = "cuda:0"
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(0)
+    ctx = rmg.Context(0, stream.cuda_stream)
+    rows = []
+    for (cx, cy), paper in PAPER_TABLE4.items():
+        p = W.q1_laplace2d_box(3 * cx - 2, 3 * cy - 2, rhs=False)
+        dp = upload(p, dev, with_rhs=False)
+        lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+        lay.operator_from_csr(9, dp.rowptr, dp.col, dp.val)
+        h = rmg.Hierarchy(lay, rmg.default_options(levels=2))
+        n_r = p.n_regional_nodes
+        wr = torch.empty(3 * n_r, dtype=torch.float32, device=dev)
+        row = {"coarse_mesh": f"{cx}x{cy}", "fine_mesh": f"{3 * cx - 2}x{3 * cy - 2}"}
+        for kind in ("const", "geo", "generic"):
+            if kind == "geo":
+                h.set_transfer_weights(0, None)
+            elif kind == "const":
+                h.constant_weights(0, wr)
+                h.set_transfer_weights(0, wr)
+            else:
+                g = np.random.default_rng(11).uniform(0.05, 0.95, 3 * n_r).astype(np.float32)
+                wr.copy_(torch.from_numpy(g))
+                h.set_transfer_weights(0, wr)
+            h.setup_numeric()
+            for _ in range(2):
+                h.galerkin(0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                h.galerkin(0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[f"{kind}_ms"] = round(ms, 4)
+            row[f"{kind}_speedup_vs_paper_structured"] = round(paper[kind] * 1e3 / ms, 1)
+        row["paper_cpu_serial_s"] = paper
+        rows.append(row)
+        h.close()
+        lay.close()
+        del dp
+        torch.cuda.empty_cache()
+    out = {"metric": "Galerkin triple product time, 2D 9-point operator, one region "
+                     "(the meshes of the paper's Table 4)",
+           "unit": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+           "rows": rows,
+           "note": "Const and Generic run the stored-weight kernels, Geo the implicit linear "
+                   "weights; the paper's times are serial CPU (Trilinos/MueLu and its structured "
+                   "kernels), context only"}
+    print(json.dumps(out))
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(json.dumps(out) + "\n")
 
 
 def reference_arm(args, cfg):

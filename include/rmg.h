@@ -335,6 +335,19 @@ rmg_status rmg_hier_level_export(rmg_hier* hier, int level, double* coeffs, doub
                                  int64_t* gids);
 /* Chebyshev lambda~ estimate of a level (host). */
 rmg_status rmg_hier_lambda(rmg_hier* hier, int level, double* lam);
+/* Recompute the Galerkin product [[Abar]] = [[R]] [[A]] [[P]] of level -> level + 1 alone
+ * (eq. RegionalGalerkinProduct; the level's current transfer: linear, or the stored weights of
+ * rmg_hier_set_transfer_weights), exactly as rmg_setup_numeric computes it, on the context's
+ * stream. For timing the triple product (Table 4) or refreshing one coarse operator; the
+ * diagonals, lambda and the coarse factor are not refreshed. RMG_ERR_ARG for a level outside
+ * 0 .. levels-2.
+ *
+ * A hierarchy whose coarsest level has more than 16384 unknowns (RMG_MAX_DENSE) is built
+ * without the dense coarse solver: setup, this call and the introspection calls work, while
+ * cycles and solves fail with RMG_ERR_STATE. */
+#define RMG_MAX_DENSE 16384
+rmg_status rmg_hier_galerkin(rmg_hier* hier, int level);
+
 /* Tile shape the stencil sweeps of a level use (see RMG_NUM_TILE_SHAPES): the box extents, or
  * 0, 0, 0 for runs of 256 nodes (also for the coarsest level, which is not smoothed). Host
  * ints; fails with RMG_ERR_ARG for a level outside the hierarchy. */

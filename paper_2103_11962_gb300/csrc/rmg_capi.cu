@@ -292,6 +292,11 @@ rmg_status rmg_hier_convergence_factor(rmg_hier* hh, int iters, unsigned long lo
   });
 }
 
+rmg_status rmg_hier_galerkin(rmg_hier* hh, int level) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] { galerkin_level(hh->h, level); });
+}
+
 rmg_status rmg_hier_constant_weights(rmg_hier* hh, int level, float* wr) {
   if (!hh) return RMG_ERR_ARG;
   return guarded(hh->h.layout->ctx, [&] {

@@ -595,8 +595,9 @@ void hier_build(Hier& h) {
   RMG_LAUNCHED();
   h.nc = exclusive_scan(c, freeflag.get(), pos.get(), Lc.ncomp);
   const long long ncd = (long long)h.nc * Lc.B;
-  RMG_REQUIRE(ncd * ncd < (1LL << 31), RMG_ERR_ARG,
-              "coarsest level too large for the dense solver (add levels)");
+  // a coarsest level above the dense solver's size leaves a hierarchy for setup and
+  // introspection only (cycles fail with RMG_ERR_STATE)
+  h.dense_ok = ncd <= kMaxDense;
   h.cidx.alloc(Lc.ncomp);
   h.cu2slot.alloc(std::max(1, h.nc));
   h.cu2gid.alloc(std::max(1, h.nc));
@@ -604,7 +605,7 @@ void hier_build(Hier& h) {
       Lc.ncomp, freeflag.get(), pos.get(), Lc.c2r.get(), h.cidx.get(), h.cu2slot.get(),
       h.cu2gid.get());
   RMG_LAUNCHED();
-  const size_t nd = (size_t)std::max(1LL, ncd);
+  const size_t nd = h.dense_ok ? (size_t)std::max(1LL, ncd) : 1;
   h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd); h.Linv.alloc(nd * nd);
   h.Tinv.alloc(nd * nd);
   h.Dblk.alloc((size_t)((nd + kNB - 1) / kNB) * kNB * kNB);
@@ -704,6 +705,14 @@ static void galerkin(Hier& h, int l, Level& F, Level& C) {
   const int g = persistent_grid(*h.c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
   k_convert<float, double><<<g, 256, 0, h.c->stream>>>(nco, C.coef32.get(), C.coef.get());
   RMG_LAUNCHED();
+}
+
+// Recompute the Galerkin product of level -> level + 1 alone (with the level's current
+// transfer), as the numeric setup does it.
+void galerkin_level(Hier& h, int level) {
+  RMG_REQUIRE(level >= 0 && level + 1 < h.levels(), RMG_ERR_ARG,
+              "Galerkin products exist for levels 0 .. levels-2");
+  galerkin(h, level, *h.lv[level], *h.lv[level + 1]);
 }
 
 // Stored transfer weights for level -> level+1 (NULL restores linear interpolation). The
@@ -851,7 +860,7 @@ static void coarse_factor(Hier& h) {
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   Level& L = *h.lv[h.levels() - 1];
-  if (h.nc == 0) return;
+  if (h.nc == 0 || !h.dense_ok) return;
   const int nc = h.nc * L.B;     // dense dimension: B dofs per free composite node
   RMG_CUDA(cudaMemsetAsync(h.Mfac.get(), 0, (size_t)nc * nc * sizeof(double), st));
   const dim3 gb(persistent_grid(c, (L.ncomp + 127) / 128), L.B);
@@ -1071,7 +1080,7 @@ void hier_numeric(Hier& h) {
     h.graph = nullptr;
   }
   h.graph_stored = stored;
-  if (h.o.use_graph && !h.gexec) {
+  if (h.o.use_graph && !h.gexec && h.dense_ok) {
     if (!h.graph_stream) RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
     RMG_CUDA(cudaStreamBeginCapture(h.graph_stream, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
@@ -1092,7 +1101,14 @@ void hier_numeric(Hier& h) {
   }
 }
 
+void require_dense(const Hier& h) {
+  RMG_REQUIRE(h.dense_ok, RMG_ERR_STATE,
+              "the coarsest level has more unknowns than the dense coarse solver takes (" +
+                  std::to_string(kMaxDense) + "); use more levels");
+}
+
 void vcycle(Hier& h) {
+  require_dense(h);
   h.probe_pending = h.levels() > 1 && (h.o.nu2 > 0);
   if (h.gexec) {
     RMG_CUDA(cudaGraphLaunch(h.gexec, h.c->stream));
@@ -1143,6 +1159,7 @@ void probe_collect(Hier& h) {
 // e <- e - M^-1 A e. Returns (||e_K||_A / ||e_0||_A)^(1/K), the mean A-norm error reduction
 // per cycle (FP64 A-norm; the cycle in the hierarchy's own precision).
 double convergence_factor(Hier& h, int iters, unsigned long long seed) {
+  require_dense(h);
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   const Level& L0 = *h.lv[0];
@@ -1183,6 +1200,7 @@ double convergence_factor(Hier& h, int iters, unsigned long long seed) {
 // ---------------------------------------------------------------------- PCG
 void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, double* history,
                rmg_solve_info* info) {
+  require_dense(h);
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
   const Level& L0 = *h.lv[0];

@@ -56,6 +56,7 @@ struct Hier {
   std::vector<DBuf<Tile>> stiles;
   std::vector<Grid> sgrid;
   bool tuned = false;
+  bool dense_ok = true;                      // coarsest level within the dense solver
   int kind0 = 0;                             // level-0 stencil and buffer seen by the graph
   const double* coef0 = nullptr;
   // probe: CUDA events around one level-0 smoother stencil launch of every V-cycle
@@ -80,8 +81,11 @@ struct Hier {
 };
 
 void hier_build(Hier& h);          // symbolic: coarse layouts, buffers
-void hier_numeric(Hier& h);
-void tile_shape(const Hier& h, int level, int* tx, int* ty, int* tz);        // numeric: diagonals, RAP, lambda, coarse factor, graph
+void hier_numeric(Hier& h);        // numeric: diagonals, RAP, lambda, coarse factor, graph
+void tile_shape(const Hier& h, int level, int* tx, int* ty, int* tz);
+void galerkin_level(Hier& h, int level);   // one Galerkin product, level -> level + 1
+// Largest dense coarse system (unknowns) the coarse solver factors.
+constexpr long long kMaxDense = 16384;
 void probe_collect(Hier& h);       // read the probe events of the last V-cycle
 void vcycle(Hier& h);              // lv[0] rhs in v64[0].b (or v32[0].b) -> result in .u
 void vcycle_apply(Hier& h, const double* r, double* z, int regional);

@@ -87,6 +87,7 @@ def lib():
                                                 ctypes.POINTER(ctypes.c_int)]),
         "rmg_hier_level_export": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "rmg_hier_lambda": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "rmg_hier_galerkin": (ctypes.c_int, [P, ctypes.c_int]),
         "rmg_hier_tile_shape": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]),
@@ -134,7 +135,7 @@ def exported_symbols():
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
             "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
             "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor",
-            "rmg_hier_tile_shape", "rmg_mlp_num_params", "rmg_mlp_create",
+            "rmg_hier_tile_shape", "rmg_hier_galerkin", "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
             "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
 
@@ -307,6 +308,10 @@ class Hierarchy:
     def level_export(self, level, coeffs=None, dinv=None, gids=None):
         self.ctx.check(lib().rmg_hier_level_export(self.h, level, _ptr(coeffs), _ptr(dinv),
                                                    _ptr(gids)))
+
+    def galerkin(self, level):
+        """Recompute the Galerkin product of level -> level + 1 alone (asynchronous)."""
+        self.ctx.check(lib().rmg_hier_galerkin(self.h, level))
 
     def tile_shape(self, level):
         """(tx, ty, tz) of the level's stencil-sweep tiles; (0, 0, 0) for runs of 256 nodes."""

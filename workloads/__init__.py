@@ -374,6 +374,27 @@ def q1_laplace2d(region_grid=(2, 2), n=28, seed=0, rhs=True):
 # ----------------------------------------------------------------------------------------
 # named configurations
 
+def q1_laplace2d_box(nx, ny, seed=0, rhs=True):
+    """2D Q1 Laplacian (9-point) on one region of nx x ny nodes (the single-region meshes of
+    the triple-product timings, Table 4)."""
+    slabs = ([nx], [ny], [1])
+    gdims, rdims, gids = region_map(slabs)
+    Nx, Ny, Nz = gdims
+    vals = np.zeros((9, Nz, Ny, Nx))
+    Ke = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0
+    corners = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    for a, (ax, ay) in enumerate(corners):
+        for c, (cx, cy) in enumerate(corners):
+            s = (cx - ax + 1) + 3 * (cy - ay + 1)
+            vals[s, 0, ay:ay + Ny - 1, ax:ax + Nx - 1] += Ke[a, c]
+    mask = boundary_mask(gdims)
+    A = _csr_from_stencil(gdims, OFFS9, vals, mask)
+    rng = np.random.default_rng(seed)
+    b = _rhs(rng, A.shape[0], mask) if rhs else np.zeros(A.shape[0])
+    return Problem("q1_laplace2d_box", 2, 1, gdims, slabs, rdims, gids, mask, A, b, 9,
+                   dict(seed=seed, nx=nx, ny=ny))
+
+
 def config(name: str, **kw) -> Problem:
     """The five paper-shaped workloads by name, with optional size overrides."""
     if name == "c1_poisson2d":
