@@ -17,6 +17,9 @@ Hier::~Hier() {
   for (auto e : probe_ev) if (e) cudaEventDestroy(e);
 }
 
+// the mixed-precision dense coarse solve (defined with the coarse factorisation below)
+static int mixed_coarse_solve(Hier& h, cudaStream_t st, int nd, int steps, double* nrm);
+
 namespace {
 
 template <typename T>
@@ -58,6 +61,76 @@ __global__ void k_gemv(int nc, const double* __restrict__ A, const double* __res
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) out[i] = s;
   }
+}
+
+// ---- mixed-precision dense coarse solve ------------------------------------------------
+// s_i = 1 / sqrt(Abar_ii): the symmetric diagonal scaling that takes the coefficient contrast
+// out of the coarse matrix before it is factored in FP32.
+__global__ void k_dense_scale(int nd, const double* __restrict__ A, double* __restrict__ s) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x)
+    s[i] = 1.0 / sqrt(A[(size_t)i * nd + i]);
+}
+
+// M = S A S rounded to FP32 (row blockIdx.y).
+__global__ void k_dense_scaled32(int nd, const double* __restrict__ A,
+                                 const double* __restrict__ s, float* __restrict__ M) {
+  const int i = blockIdx.y;
+  const double si = s[i];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x)
+    M[(size_t)i * nd + j] = (float)(si * A[(size_t)i * nd + j] * s[j]);
+}
+
+// w = FP32(s .* r)
+__global__ void k_scale_vec32(int nd, const double* __restrict__ s, const double* __restrict__ r,
+                              float* __restrict__ w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x)
+    w[i] = (float)(s[i] * r[i]);
+}
+
+// x = s .* (M w) (accumulate = 0) or x += s .* (M w): one warp per row, FP32 products and sums.
+__global__ void k_gemv32(int nd, const float* __restrict__ M, const float* __restrict__ w,
+                         const double* __restrict__ s, double* __restrict__ x, int accumulate) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < nd; i += nwarps) {
+    float acc = 0.f;
+    const float* row = M + (size_t)i * nd;
+    for (int j = lane; j < nd; j += 32) acc = fmaf(row[j], w[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[i] = (accumulate ? x[i] : 0.0) + s[i] * (double)acc;
+  }
+}
+
+// res = rc - A x in FP64: one warp per row.
+__global__ void k_resid_dense(int nd, const double* __restrict__ A, const double* __restrict__ x,
+                              const double* __restrict__ rc, double* __restrict__ res) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < nd; i += nwarps) {
+    double acc = 0.0;
+    const double* row = A + (size_t)i * nd;
+    for (int j = lane; j < nd; j += 32) acc = fma(row[j], x[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) res[i] = rc[i] - acc;
+  }
+}
+
+// out[0] = sum v^2 (one block).
+__global__ void k_norm2_dense(int nd, const double* __restrict__ v, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) acc = fma(v[i], v[i], acc);
+  acc = block_sum<256>(acc);
+  if (threadIdx.x == 0) out[0] = acc;
+}
+
+// SplitMix64 test vector for measuring the refinement's contraction.
+__global__ void k_dense_random(int nd, unsigned long long seed, double* __restrict__ v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x)
+    v[i] = splitmix_pm1(seed, (unsigned long long)i);
 }
 
 template <typename VT>
@@ -401,10 +474,14 @@ struct Exec {
                                                                 h.cu2slot.get(), h.rc.get());
       RMG_LAUNCHED();
       const int nd = nc * L.B;
-      const int blocks = std::max(1, std::min(c().nsm * 4, (nd * 32 + 255) / 256));
-      k_gemv<<<blocks, 256, 0, st>>>(nd, h.Ainv.get(), h.rc.get(), h.xc.get());
-      RMG_LAUNCHED();
-      launches += 2;
+      if (h.coarse_refine > 0) {
+        launches += 1 + mixed_coarse_solve(h, st, nd, h.coarse_refine, nullptr);
+      } else {
+        const int blocks = std::max(1, std::min(c().nsm * 4, (nd * 32 + 255) / 256));
+        k_gemv<<<blocks, 256, 0, st>>>(nd, h.Ainv.get(), h.rc.get(), h.xc.get());
+        RMG_LAUNCHED();
+        launches += 2;
+      }
     }
     k_coarse_scatter<VT><<<elementwise_grid(L.n_r), 256, 0, st>>>(L.n_r, L.B, L.gid.get(),
                                                                   h.cidx.get(), h.xc.get(), cur[l]);
@@ -606,9 +683,13 @@ void hier_build(Hier& h) {
       h.cu2gid.get());
   RMG_LAUNCHED();
   const size_t nd = h.dense_ok ? (size_t)std::max(1LL, ncd) : 1;
+  const size_t nblk = (nd + kNB - 1) / kNB;
   h.Mfac.alloc(nd * nd); h.X.alloc(nd * nd); h.Ainv.alloc(nd * nd); h.Linv.alloc(nd * nd);
   h.Tinv.alloc(nd * nd);
-  h.Dblk.alloc((size_t)((nd + kNB - 1) / kNB) * kNB * kNB);
+  h.Dblk.alloc(nblk * kNB * kNB);
+  h.M32.alloc(nd * nd); h.Ainv32.alloc(nd * nd); h.Linv32.alloc(nd * nd); h.Tinv32.alloc(nd * nd);
+  h.Dblk32.alloc(nblk * kNB * kNB);
+  h.cscale.alloc(nd); h.cres.alloc(nd); h.cw32.alloc(nd); h.cnorm.alloc(4); h.cerr.alloc(1);
   h.xc.alloc(nd); h.rc.alloc(nd);
   RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
@@ -856,6 +937,9 @@ static void power_method(Hier& h, int l) {
   }
 }
 
+static bool coarse_factor_mixed(Hier& h, int nd);
+static void coarse_factor_fp64(Hier& h, int nc);
+
 static void coarse_factor(Hier& h) {
   Ctx& c = *h.c;
   cudaStream_t st = c.stream;
@@ -877,40 +961,129 @@ static void coarse_factor(Hier& h) {
   }
 #undef RMG_ASM
   RMG_LAUNCHED();
-  // keep the assembled matrix for introspection in X before factorising
+  // keep the assembled matrix for introspection and for the refinement residuals in X
   RMG_CUDA(cudaMemcpyAsync(h.X.get(), h.Mfac.get(), (size_t)nc * nc * sizeof(double),
                            cudaMemcpyDeviceToDevice, st));
-  for (int k0 = 0; k0 < nc; k0 += kNB) {
-    k_chol_diag<<<1, 32, 0, st>>>(h.Mfac.get(), nc, k0, h.Dblk.get(), c.d_err.get());
+  if (!coarse_factor_mixed(h, nc)) coarse_factor_fp64(h, nc);
+}
+
+// Dense inverse in precision F of the nd x nd matrix in M (overwritten by its Cholesky factor):
+// blocked Cholesky, L^-1 by recursive doubling, Ainv = L^-T L^-1.
+template <typename F>
+static void dense_inverse(Ctx& c, cudaStream_t st, int nd, F* M, F* Dblk, F* Linv, F* Tinv,
+                          F* Ainv, int* err) {
+  for (int k0 = 0; k0 < nd; k0 += kNB) {
+    k_chol_diag<F><<<1, 32, 0, st>>>(M, nd, k0, Dblk, err);
     RMG_LAUNCHED();
-    const int k1 = std::min(nc, k0 + kNB);
-    if (k1 < nc) {
-      const int rows = nc - k1;
-      k_chol_panel<<<std::min(1024, (rows + 7) / 8), 256, 0, st>>>(h.Mfac.get(), nc, k0,
-                                                                  h.Dblk.get());
+    const int k1 = std::min(nd, k0 + kNB);
+    if (k1 < nd) {
+      const int rows = nd - k1;
+      k_chol_panel<F><<<std::min(1024, (rows + 7) / 8), 256, 0, st>>>(M, nd, k0, Dblk);
       RMG_LAUNCHED();
       const int tiles = (rows + 15) / 16;
-      k_chol_update<<<dim3(tiles, tiles), dim3(16, 16), 0, st>>>(h.Mfac.get(), nc, k0, k1);
+      k_chol_update<F><<<dim3(tiles, tiles), dim3(16, 16), 0, st>>>(M, nd, k0, k1);
       RMG_LAUNCHED();
     }
   }
-  c.check_device_error("rmg_setup (coarse factorisation)");
-  // X = L^-1 by recursive doubling from the inverted diagonal blocks, then Ainv = X^T X
-  RMG_CUDA(cudaMemsetAsync(h.Linv.get(), 0, (size_t)nc * nc * sizeof(double), st));
-  const int nblk = (nc + kNB - 1) / kNB;
-  k_inv_diag_blocks<<<nblk, 256, 0, st>>>(nc, h.Dblk.get(), h.Linv.get());
+  RMG_CUDA(cudaMemsetAsync(Linv, 0, (size_t)nd * nd * sizeof(F), st));
+  const int nblk = (nd + kNB - 1) / kNB;
+  k_inv_diag_blocks<F><<<nblk, 256, 0, st>>>(nd, Dblk, Linv);
   RMG_LAUNCHED();
-  for (int s = kNB; s < nc; s *= 2) {
-    const int tiles = (s + kNB - 1) / kNB, pairs = (nc + 2 * s - 1) / (2 * s);
+  for (int s = kNB; s < nd; s *= 2) {
+    const int tiles = (s + kNB - 1) / kNB, pairs = (nd + 2 * s - 1) / (2 * s);
     const dim3 grid(tiles, tiles, pairs);
-    k_inv_merge<1><<<grid, 256, 0, st>>>(h.Mfac.get(), h.Linv.get(), h.Tinv.get(), nc, s);
+    k_inv_merge<1, F><<<grid, 256, 0, st>>>(M, Linv, Tinv, nd, s);
     RMG_LAUNCHED();
-    k_inv_merge<2><<<grid, 256, 0, st>>>(h.Mfac.get(), h.Linv.get(), h.Tinv.get(), nc, s);
+    k_inv_merge<2, F><<<grid, 256, 0, st>>>(M, Linv, Tinv, nd, s);
     RMG_LAUNCHED();
   }
-  const int t = (nc + 15) / 16;
-  k_xtx<<<dim3(t, t), dim3(16, 16), 0, st>>>(h.Linv.get(), nc, h.Ainv.get());
+  const int t = (nd + 15) / 16;
+  k_xtx<F><<<dim3(t, t), dim3(16, 16), 0, st>>>(Linv, nd, Ainv);
   RMG_LAUNCHED();
+}
+
+static void coarse_factor_fp64(Hier& h, int nc) {
+  Ctx& c = *h.c;
+  dense_inverse<double>(c, c.stream, nc, h.Mfac.get(), h.Dblk.get(), h.Linv.get(), h.Tinv.get(),
+                        h.Ainv.get(), c.d_err.get());
+  c.check_device_error("rmg_setup (coarse factorisation)");
+  h.coarse_refine = 0;
+}
+
+// One mixed-precision coarse solve xc = Abar^-1 rc: x = S Ainv32 S rc, then `steps` FP64
+// refinement steps x += S Ainv32 S (rc - Abar x). nrm (optional) receives ||rc - Abar x||^2
+// before every refinement step.
+static int mixed_coarse_solve(Hier& h, cudaStream_t st, int nd, int steps, double* nrm) {
+  Ctx& c = *h.c;
+  const int eg = std::max(1, std::min(c.nsm * 4, (nd + 255) / 256));
+  const int wg = std::max(1, std::min(c.nsm * 4, (nd * 32 + 255) / 256));
+  int launches = 0;
+  k_scale_vec32<<<eg, 256, 0, st>>>(nd, h.cscale.get(), h.rc.get(), h.cw32.get());
+  RMG_LAUNCHED();
+  k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), h.xc.get(), 0);
+  RMG_LAUNCHED();
+  launches += 2;
+  for (int k = 0; k < steps; ++k) {
+    k_resid_dense<<<wg, 256, 0, st>>>(nd, h.X.get(), h.xc.get(), h.rc.get(), h.cres.get());
+    RMG_LAUNCHED();
+    if (nrm) {
+      k_norm2_dense<<<1, 256, 0, st>>>(nd, h.cres.get(), nrm + k);
+      RMG_LAUNCHED();
+    }
+    k_scale_vec32<<<eg, 256, 0, st>>>(nd, h.cscale.get(), h.cres.get(), h.cw32.get());
+    RMG_LAUNCHED();
+    k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), h.xc.get(),
+                                 1);
+    RMG_LAUNCHED();
+    launches += 3;
+  }
+  return launches;
+}
+
+// FP32 factorisation of S Abar S (GB300's FP32 pipe is 64x its FP64 one) with FP64 iterative
+// refinement in every coarse solve. The number of refinement steps comes from the contraction
+// measured here on a test vector (it must bring the relative residual to 1e-15); a breakdown of
+// the FP32 factorisation or a contraction above 0.1 leaves the FP64 inverse to the caller.
+static bool coarse_factor_mixed(Hier& h, int nd) {
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  const int eg = std::max(1, std::min(c.nsm * 4, (nd + 255) / 256));
+  k_dense_scale<<<eg, 256, 0, st>>>(nd, h.X.get(), h.cscale.get());
+  RMG_LAUNCHED();
+  k_dense_scaled32<<<dim3((nd + 255) / 256, nd), 256, 0, st>>>(nd, h.X.get(), h.cscale.get(),
+                                                               h.M32.get());
+  RMG_LAUNCHED();
+  RMG_CUDA(cudaMemsetAsync(h.cerr.get(), 0, sizeof(int), st));
+  dense_inverse<float>(c, st, nd, h.M32.get(), h.Dblk32.get(), h.Linv32.get(), h.Tinv32.get(),
+                       h.Ainv32.get(), h.cerr.get());
+  // contraction of the refinement on a SplitMix64 test right-hand side
+  k_dense_random<<<eg, 256, 0, st>>>(nd, 0x5eedull, h.rc.get());
+  RMG_LAUNCHED();
+  k_norm2_dense<<<1, 256, 0, st>>>(nd, h.rc.get(), h.cnorm.get());
+  RMG_LAUNCHED();
+  mixed_coarse_solve(h, st, nd, 3, h.cnorm.get() + 1);
+  int err = 0;
+  RMG_CUDA(cudaMemcpyAsync(h.pinned, h.cnorm.get(), 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                           st));
+  RMG_CUDA(cudaMemcpyAsync(&err, h.cerr.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  RMG_CUDA(cudaStreamSynchronize(st));
+  const double b2 = h.pinned[0], r0 = h.pinned[1], r1 = h.pinned[2], r2 = h.pinned[3];
+  if (err || !(b2 > 0.0) || !std::isfinite(r0) || !std::isfinite(r2) || !(r0 > 0.0)) return false;
+  // per-step contraction from the last two steps (the first one also removes the FP32
+  // rounding of the right-hand side), in norms
+  const double rho = std::sqrt(std::max(r2, 1e-300) / std::max(r1, 1e-300));
+  const double rel0 = std::sqrt(r0 / b2);
+  if (!(rho < 0.1)) return false;
+  int steps = 1;
+  double rel = rel0 * std::max(rho, 1e-16);
+  while (rel > 1e-15 && steps < 8) {
+    rel *= std::max(rho, 1e-16);
+    ++steps;
+  }
+  if (rel > 1e-15) return false;
+  h.coarse_rho = rho;
+  h.coarse_refine = steps;
+  return true;
 }
 
 // FP32 copy of the level-0 coefficients for the mixed hierarchy's FP32 Galerkin chain.
@@ -1073,13 +1246,14 @@ void hier_numeric(Hier& h) {
   RMG_CUDA(cudaMemcpyAsync(&h.hsc, h.sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
   const std::vector<char>& stored = h.stored;
-  if (h.gexec && stored != h.graph_stored) {
+  if (h.gexec && (stored != h.graph_stored || h.coarse_refine != h.graph_refine)) {
     cudaGraphExecDestroy(h.gexec);
     cudaGraphDestroy(h.graph);
     h.gexec = nullptr;
     h.graph = nullptr;
   }
   h.graph_stored = stored;
+  h.graph_refine = h.coarse_refine;
   if (h.o.use_graph && !h.gexec && h.dense_ok) {
     if (!h.graph_stream) RMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
     RMG_CUDA(cudaStreamBeginCapture(h.graph_stream, cudaStreamCaptureModeThreadLocal));

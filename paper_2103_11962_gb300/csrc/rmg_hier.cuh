@@ -40,6 +40,14 @@ struct Hier {
   DBuf<long long> cu2gid;
   DBuf<double> Mfac, X, Ainv, xc, rc;
   DBuf<double> Linv, Dblk, Tinv;             // L^-1, inverted 32 x 32 diagonal blocks, scratch
+  // mixed-precision coarse solve: FP32 inverse of S Abar S (S = diag(Abar)^-1/2) and
+  // coarse_refine FP64 refinement steps per solve; coarse_refine = 0: the FP64 inverse Ainv
+  DBuf<double> cscale, cres, cnorm;
+  DBuf<float> M32, Ainv32, Linv32, Tinv32, Dblk32, cw32;
+  DBuf<int> cerr;
+  int coarse_refine = 0;
+  int graph_refine = -1;                     // coarse_refine the graph was captured with
+  double coarse_rho = 0.0;                   // measured contraction of one refinement step
   // graph of one V-cycle
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;

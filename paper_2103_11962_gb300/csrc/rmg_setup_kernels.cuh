@@ -478,76 +478,80 @@ __global__ void k_coarse_assemble(int ncomp, int B, const RegionDev* __restrict_
 // A partial last block is padded with the identity inside the kernels.
 constexpr int kNB = 32;
 
+template <typename F>
 __global__ void __launch_bounds__(32)
-k_chol_diag(double* M, int n, int k0, double* __restrict__ Dblk, int* err) {
-  __shared__ double T[kNB][kNB + 1];
-  __shared__ double X[kNB][kNB + 1];
-  __shared__ double rdiag[kNB];
+k_chol_diag(F* M, int n, int k0, F* __restrict__ Dblk, int* err) {
+  __shared__ F T[kNB][kNB + 1];
+  __shared__ F X[kNB][kNB + 1];
+  __shared__ F rdiag[kNB];
   const int nb = min(kNB, n - k0);
   const int ln = threadIdx.x;
   for (int i = 0; i < kNB; ++i)
-    T[i][ln] = (i < nb && ln < nb) ? M[(size_t)(k0 + i) * n + k0 + ln] : (i == ln ? 1.0 : 0.0);
+    T[i][ln] = (i < nb && ln < nb) ? M[(size_t)(k0 + i) * n + k0 + ln] : F(i == ln ? 1 : 0);
   __syncwarp();
   for (int j = 0; j < kNB; ++j) {
-    double p = T[j][j];
-    if (!(p > 0.0)) {
+    F p = T[j][j];
+    if (!(p > F(0))) {
       if (ln == 0) set_err(err, DERR_NOT_SPD);
-      p = 1.0;
+      p = F(1);
     }
     // 1/sqrt(p): FP32 seed, then two Newton steps in FP64 (relative error 1e-7 -> 1e-14 ->
     // rounding), far shorter on the FP64 pipe than a sqrt and a division; pivots outside the
     // FP32 range take the sqrt and the division
-    double rd;
-    if (p > 1e-30 && p < 1e30) {
-      rd = (double)rsqrtf((float)p);
-      rd = rd * (1.5 - 0.5 * p * rd * rd);
-      rd = rd * (1.5 - 0.5 * p * rd * rd);
+    F rd;
+    if (sizeof(F) == 4) {
+      rd = F(rsqrtf((float)p));
+    } else if (p > F(1e-30) && p < F(1e30)) {
+      rd = F(rsqrtf((float)p));
+      rd = rd * (F(1.5) - F(0.5) * p * rd * rd);
+      rd = rd * (F(1.5) - F(0.5) * p * rd * rd);
     } else {
-      rd = 1.0 / sqrt(p);
+      rd = F(1) / sqrt(p);
     }
-    const double d = p * rd;
+    const F d = p * rd;
     __syncwarp();
     if (ln == j) { T[j][j] = d; rdiag[j] = rd; }
     if (ln > j) T[ln][j] *= rd;
     __syncwarp();
     if (ln > j) {
-      const double lij = T[ln][j];
+      const F lij = T[ln][j];
       for (int c = j + 1; c <= ln; ++c) T[ln][c] -= lij * T[c][j];
     }
     __syncwarp();
   }
   // column ln of L^-1 by forward substitution (each lane owns one column)
   for (int i = 0; i < kNB; ++i) {
-    double x = 0.0;
+    F x = F(0);
     if (i >= ln) {
-      double s = i == ln ? 1.0 : 0.0;
+      F s = F(i == ln ? 1 : 0);
       for (int m = ln; m < i; ++m) s -= T[i][m] * X[m][ln];
       x = s * rdiag[i];
     }
     X[i][ln] = x;
   }
   __syncwarp();
-  double* D = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
+  F* D = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
   for (int i = 0; i < kNB; ++i) {
     D[i * kNB + ln] = X[i][ln];
-    if (i < nb && ln < nb) M[(size_t)(k0 + i) * n + k0 + ln] = ln <= i ? T[i][ln] : 0.0;
+    if (i < nb && ln < nb) M[(size_t)(k0 + i) * n + k0 + ln] = ln <= i ? T[i][ln] : F(0);
   }
 }
 
+template <typename F>
 __global__ void __launch_bounds__(256)
-k_chol_panel(double* M, int n, int k0, const double* __restrict__ Dblk) {
-  __shared__ double D[kNB][kNB + 1], A[8][kNB + 1];
+k_chol_panel(F* M, int n, int k0, const F* __restrict__ Dblk) {
+  __shared__ F D[kNB][kNB + 1], A[8][kNB + 1];
   const int nb = min(kNB, n - k0);
-  const double* Dk = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
+  const F* Dk = Dblk + (size_t)(k0 / kNB) * kNB * kNB;
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) D[e / kNB][e % kNB] = Dk[e];
   const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
   for (int rb = k0 + nb + blockIdx.x * 8; rb < n; rb += gridDim.x * 8) {
     __syncthreads();
     const int r = rb + tr;
-    A[tr][tc] = (r < n && tc < nb) ? M[(size_t)r * n + k0 + tc] : 0.0;
+    A[tr][tc] = (r < n && tc < nb) ? M[(size_t)r * n + k0 + tc] : F(0);
     __syncthreads();
     if (r < n && tc < nb) {
-      double s = 0.0;
+      F s = F(0);
       for (int m = 0; m <= tc; ++m) s = fma(A[tr][m], D[tc][m], s);
       M[(size_t)r * n + k0 + tc] = s;
     }
@@ -555,8 +559,9 @@ k_chol_panel(double* M, int n, int k0, const double* __restrict__ Dblk) {
 }
 
 // Trailing update of the lower triangle: M[i][j] -= sum_k L[i][k] L[j][k], i, j >= k1.
-__global__ void k_chol_update(double* M, int n, int k0, int k1) {
-  __shared__ double Li[16][kNB + 1], Lj[16][kNB + 1];
+template <typename F>
+__global__ void k_chol_update(F* M, int n, int k0, int k1) {
+  __shared__ F Li[16][kNB + 1], Lj[16][kNB + 1];
   const int ti = blockIdx.y * 16, tj = blockIdx.x * 16;
   if (tj > ti + 15) return;     // tile strictly above the diagonal
   const int nb = k1 - k0;
@@ -564,13 +569,13 @@ __global__ void k_chol_update(double* M, int n, int k0, int k1) {
   for (int e = ty * 16 + tx; e < 16 * kNB; e += 256) {
     const int r = e / kNB, k = e % kNB;
     const int gi = k1 + ti + r, gj = k1 + tj + r;
-    Li[r][k] = (gi < n && k < nb) ? M[(size_t)gi * n + k0 + k] : 0.0;
-    Lj[r][k] = (gj < n && k < nb) ? M[(size_t)gj * n + k0 + k] : 0.0;
+    Li[r][k] = (gi < n && k < nb) ? M[(size_t)gi * n + k0 + k] : F(0);
+    Lj[r][k] = (gj < n && k < nb) ? M[(size_t)gj * n + k0 + k] : F(0);
   }
   __syncthreads();
   const int i = k1 + ti + ty, j = k1 + tj + tx;
   if (i < n && j < n && j <= i) {
-    double s = 0.0;
+    F s = F(0);
     for (int k = 0; k < nb; ++k) s += Li[ty][k] * Lj[tx][k];
     M[(size_t)i * n + j] -= s;
   }
@@ -584,10 +589,11 @@ __global__ void k_chol_update(double* M, int n, int k0, int k1) {
 //   step 2: X21 = -X22 T  (X22 lower: output row tile rt needs k < 32 (rt + 1) only)
 // All pairs of a level run in one launch (blockIdx.z), so every launch fills the GPU with
 // 32 x 32 output tiles; thread (ty, tx) owns rows ty, ty + 8, ty + 16, ty + 24 of column tx.
+template <typename F>
 __global__ void __launch_bounds__(256)
-k_inv_diag_blocks(int n, const double* __restrict__ Dblk, double* __restrict__ X) {
+k_inv_diag_blocks(int n, const F* __restrict__ Dblk, F* __restrict__ X) {
   const int b = blockIdx.x, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const double* D = Dblk + (size_t)b * kNB * kNB;
+  const F* D = Dblk + (size_t)b * kNB * kNB;
   for (int q = 0; q < 4; ++q) {
     const int r = ty + 8 * q;
     if (b * kNB + r < n && b * kNB + tx < n)
@@ -595,11 +601,10 @@ k_inv_diag_blocks(int n, const double* __restrict__ Dblk, double* __restrict__ X
   }
 }
 
-template <int STEP>
+template <int STEP, typename F>
 __global__ void __launch_bounds__(256)
-k_inv_merge(const double* __restrict__ L, double* __restrict__ X, double* __restrict__ T, int n,
-            int s) {
-  __shared__ double As[kNB][kNB + 1], Bs[kNB][kNB + 1];
+k_inv_merge(const F* __restrict__ L, F* __restrict__ X, F* __restrict__ T, int n, int s) {
+  __shared__ F As[kNB][kNB + 1], Bs[kNB][kNB + 1];
   const int p = blockIdx.z * 2 * s;
   const int s2 = min(s, n - p - s);
   const int rt = blockIdx.y, ct = blockIdx.x;
@@ -607,24 +612,24 @@ k_inv_merge(const double* __restrict__ L, double* __restrict__ X, double* __rest
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int kb = STEP == 1 ? ct * kNB : 0;
   const int ke = STEP == 1 ? s : min(s2, (rt + 1) * kNB);
-  const double* A = STEP == 1 ? L : X;           // rows p + s + ..., k-columns from a0
-  const double* B = STEP == 1 ? X : T;           // k-rows from a0, columns p + ...
+  const F* A = STEP == 1 ? L : X;                // rows p + s + ..., k-columns from a0
+  const F* B = STEP == 1 ? X : T;                // k-rows from a0, columns p + ...
   const int a0 = STEP == 1 ? p : p + s;
   const int r0 = p + s + rt * kNB, c0 = p + ct * kNB;
   const bool col_ok = ct * kNB + tx < s;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  F acc[4] = {F(0), F(0), F(0), F(0)};
   for (int k0 = kb; k0 < ke; k0 += kNB) {
     __syncthreads();
     for (int q = 0; q < 4; ++q) {
       const int rr = ty + 8 * q;
       As[rr][tx] = (rt * kNB + rr < s2 && k0 + tx < ke)
-                       ? A[(size_t)(r0 + rr) * n + a0 + k0 + tx] : 0.0;
-      Bs[rr][tx] = (k0 + rr < ke && col_ok) ? B[(size_t)(a0 + k0 + rr) * n + c0 + tx] : 0.0;
+                       ? A[(size_t)(r0 + rr) * n + a0 + k0 + tx] : F(0);
+      Bs[rr][tx] = (k0 + rr < ke && col_ok) ? B[(size_t)(a0 + k0 + rr) * n + c0 + tx] : F(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int m = 0; m < kNB; ++m) {
-      const double bv = Bs[m][tx];
+      const F bv = Bs[m][tx];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][m], bv, acc[q]);
     }
@@ -640,15 +645,16 @@ k_inv_merge(const double* __restrict__ L, double* __restrict__ X, double* __rest
 
 // Ainv = X^T X with X = L^-1 lower: Ainv[i][j] = sum_{k >= max(i, j)} X[k][i] X[k][j]. Lower
 // tiles are computed and mirrored, so Ainv is exactly symmetric.
-__global__ void k_xtx(const double* __restrict__ X, int n, double* __restrict__ Ainv) {
-  __shared__ double A[16][17], B[16][17];
+template <typename F>
+__global__ void k_xtx(const F* __restrict__ X, int n, F* __restrict__ Ainv) {
+  __shared__ F A[16][17], B[16][17];
   const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
   if (j0 > i0) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  double s = 0.0;
+  F s = F(0);
   for (int k0 = i0; k0 < n; k0 += 16) {
-    A[ty][tx] = (k0 + ty < n && i0 + tx < n) ? X[(size_t)(k0 + ty) * n + i0 + tx] : 0.0;
-    B[ty][tx] = (k0 + ty < n && j0 + tx < n) ? X[(size_t)(k0 + ty) * n + j0 + tx] : 0.0;
+    A[ty][tx] = (k0 + ty < n && i0 + tx < n) ? X[(size_t)(k0 + ty) * n + i0 + tx] : F(0);
+    B[ty][tx] = (k0 + ty < n && j0 + tx < n) ? X[(size_t)(k0 + ty) * n + j0 + tx] : F(0);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) s = fma(A[k][ty], B[k][tx], s);
