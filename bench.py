@@ -228,18 +228,39 @@ import numpy as np
 import workloads as W
 from oracle import cycle, hierarchy, krylov
 w = {workload!r}
-if w == 'c2_diffusion3d':
+cheb = cycle.Options(smoother='chebyshev', nu1=1, nu2=1, degree=3)
+block = False
+if w in ('c2_diffusion3d', 'c2_quarter'):
     p = W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(28, 55, 82), seed=1)
-    o = cycle.Options(smoother='chebyshev', nu1=1, nu2=1, degree=3)
+    o = cheb
     sample = 'C2-shaped 2x2x2-region instance (slabs from {{28,55,82}}, seed 1, log-normal kappa)'
+elif w.startswith('c3'):
+    p = W.q1_laplace3d(region_grid=(2, 2, 2), n=28, seed=2)
+    o = cheb
+    sample = 'C3-shaped 2x2x2-region Q1 instance (28^3 regions, seed 2)'
+elif w.startswith('c4'):
+    p = W.highcontrast3d_7pt(region_grid=(2, 2, 2), choices=(28, 55, 82), seed=3)
+    o = cheb
+    sample = 'C4-shaped 2x2x2-region high-contrast instance (slabs from {{28,55,82}}, seed 3)'
+elif w.startswith('c5'):
+    p = W.elasticity3d(region_grid=(2, 2, 2), choices=(10, 19), seed=4)
+    o = cycle.Options(smoother='chebyshev', nu1=1, nu2=1, degree=3, power_iters=30)
+    block = True
+    sample = 'C5-shaped 2x2x2-region elasticity instance (slabs from {{10,19}}, seed 4)'
 else:
     p = W.config('c1_poisson2d')
     o = cycle.Options(smoother='jacobi', nu1=2, nu2=2, omega=0.67)
     sample = 'full C1 workload'
 t0 = time.perf_counter()
-levels = hierarchy.build(p, 4)
+if block:
+    levels = hierarchy.build_block(p, 3)
+    perm = hierarchy.node_major_to_component_major(p.n_nodes, p.dofs_per_node)
+    A, b = levels[0].A, p.b[perm]
+else:
+    levels = hierarchy.build(p, 4)
+    A, b = p.A, p.b
 mg = cycle.RegionalMG(levels, o)
-x, it, hist = krylov.pcg(p.A, p.b, krylov.regional_preconditioner(mg), rtol={RTOL})
+x, it, hist = krylov.pcg(A, b, krylov.regional_preconditioner(mg), rtol={RTOL})
 t1 = time.perf_counter()
 ncyc = it if hist[-1] <= {RTOL} else it + 1
 print(json.dumps(dict(seconds=t1 - t0, iterations=it, vcycles=ncyc, unknowns=p.n_unknowns,
