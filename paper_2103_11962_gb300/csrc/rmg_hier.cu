@@ -731,8 +731,11 @@ static void galerkin_t(Hier& h, int l, const Level& F, Level& C, const T* fcoef,
   T* cco = ccoef + (size_t)blk * C.kind * C.n_r;
   const double mdiag = (blk / F.B == blk % F.B) ? 1.0 : 0.0;
 #define RMG_RAP(FK, CK, D)                                                                    \
-  {                                                                                           \
-    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(T);                         \
+  if (sizeof(T) == 4 && (FK == 5 || FK == 7)) {                                               \
+    k_ap_axis32<FK, D><<<gf, kTile, 0, c.stream>>>(Gf, C.regions.get(), (const float*)fco,     \
+                                                   F.mask.get(), C.mask.get(), (float*)ap);   \
+  } else {                                                                                    \
+    const int smem = (D == 3 ? 27 : 9) * kTile * (int)sizeof(T);                              \
     RMG_CUDA(cudaFuncSetAttribute(k_ap<FK, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   smem));                                                     \
     k_ap<FK, D, T><<<gf, kTile, smem, c.stream>>>(Gf, C.regions.get(), fco, F.mask.get(),        \

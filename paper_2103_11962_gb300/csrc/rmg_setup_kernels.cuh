@@ -127,6 +127,76 @@ k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const T* __restrict__ fcoef,
   RMG_END_FOR_NODES
 }
 
+// A P for a 5/7-point fine stencil in FP32, for the mixed hierarchies: every output o of the
+// 3 x 3 (x 3) coarse neighbourhood of f (the same ap[o][f] layout as k_ap) is evaluated
+// directly as sum_s A_s(f) wx(g_x - 3 X) wy(g_y - 3 Y) wz(g_z - 3 Z), g = f + d_s, with the
+// linear weights w(t) = 1 - |t|/3 for |t| <= 2. No divergent loops and no shared memory; the
+// 27 x 7 FMAs are cheap on the FP32 pipe (in FP64 they would not be, so the plain method
+// keeps k_ap). Masked fine neighbours and masked coarse nodes contribute nothing.
+__device__ __forceinline__ float lin_w(int t) {
+  t = t < 0 ? -t : t;
+  return t == 0 ? 1.f : (t == 1 ? 2.f / 3.f : (t == 2 ? 1.f / 3.f : 0.f));
+}
+
+template <int FK, int DIM>
+__global__ void __launch_bounds__(kTile)
+k_ap_axis32(Grid Gf, const RegionDev* __restrict__ cregs, const float* __restrict__ fcoef,
+            const uint8_t* __restrict__ fmask, const uint8_t* __restrict__ cmask,
+            float* __restrict__ ap) {
+  using FS = Sten<FK>;
+  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NZ = DIM == 3 ? 3 : 1;
+  RMG_FOR_NODES(Gf)
+    float out[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) out[o] = 0.f;
+    if (!fmask[n]) {
+      int x, y, z;
+      decode(li, R, x, y, z);
+      const int cx0 = floor_div3m1(x), cy0 = floor_div3m1(y), cz0 = DIM == 3 ? floor_div3m1(z) : 0;
+#pragma unroll
+      for (int s = 0; s < FS::S; ++s) {
+        const int dx = FS::dx(s), dy = FS::dy(s), dz = FS::dz(s);
+        const int gx = x + dx, gy = y + dy, gz = z + dz;
+        if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
+        if (fmask[R.off + gx + R.nx * (gy + R.ny * gz)]) continue;
+        const float v = fcoef[(size_t)s * Gf.n_r + n];
+        float wx[3], wy[3], wz[NZ];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          wx[k] = lin_w(gx - 3 * (cx0 + k));
+          wy[k] = lin_w(gy - 3 * (cy0 + k));
+        }
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) wz[k] = DIM == 3 ? lin_w(gz - 3 * (cz0 + k)) : 1.f;
+#pragma unroll
+        for (int kz = 0; kz < NZ; ++kz)
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky) {
+            const float vyz = v * (wz[kz] * wy[ky]);
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) out[kx + 3 * ky + 9 * kz] = fmaf(vyz, wx[kx], out[kx + 3 * ky + 9 * kz]);
+          }
+      }
+      const RegionDev C = cregs[tile_.region];
+#pragma unroll
+      for (int kz = 0; kz < NZ; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const int X = cx0 + kx, Y = cy0 + ky, Z = cz0 + kz;
+            const int o = kx + 3 * ky + 9 * kz;
+            if (X < 0 || X >= C.nx || Y < 0 || Y >= C.ny || Z < 0 || Z >= C.nz ||
+                cmask[C.off + X + C.nx * (Y + C.ny * Z)])
+              out[o] = 0.f;
+          }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) ap[(size_t)o * Gf.n_r + n] = out[o];
+  RMG_END_FOR_NODES
+}
+
 template <int DIM, bool CHECK, bool STORED, typename T>
 __device__ __forceinline__ void rtap_sum(const T* __restrict__ ap, int fn_r,
                                          const RegionDev& F, const float* __restrict__ wr,
