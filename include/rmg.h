@@ -87,6 +87,8 @@ typedef struct {
   int precision;         /* rmg_precision                                                  */
   int use_graph;         /* capture the V-cycle in a CUDA graph (1) or launch eagerly (0)  */
   int tile_shape;        /* stencil-sweep tiles: -1 autotune (default), else a shape index  */
+  int symmetric_storage; /* FP32 cycle, scalar operator: half planes of level 0 (1, default),
+                            or the full planes only (0); see rmg_hier_coef_planes           */
 } rmg_options;
 
 /* Tile shapes of the stencil sweeps (rmg_options.tile_shape, rmg_hier_tile_shape). Every
@@ -107,7 +109,8 @@ typedef struct {
 } rmg_solve_info;
 
 /* Defaults: 4 levels, Jacobi, nu1 = nu2 = 2, omega 0.67, degree 3, eig_ratio 20, boost 1.1,
- * 10 power iterations, seed base 10, FP64, graph on, tile shapes autotuned. */
+ * 10 power iterations, seed base 10, FP64, graph on, tile shapes autotuned, symmetric storage
+ * on. */
 void rmg_options_default(rmg_options* opts);
 
 /* Create a context on CUDA device `device` that queues work on `cuda_stream`
@@ -352,6 +355,17 @@ rmg_status rmg_hier_galerkin(rmg_hier* hier, int level);
  * 0, 0, 0 for runs of 256 nodes (also for the coarsest level, which is not smoothed). Host
  * ints; fails with RMG_ERR_ARG for a level outside the hierarchy. */
 rmg_status rmg_hier_tile_shape(rmg_hier* hier, int level, int* tx, int* ty, int* tz);
+/* Stencil coefficients per regional node that the cycle's sweeps read on a level, as of the
+ * last rmg_setup_numeric: B * B * S for an S-point stencil, or (S + 1) / 2 where the half form
+ * is in use. The half form (FP32 cycle, scalar operator, level 0, symmetric_storage 1) rests
+ * on the symmetry of the regional operator, a(n, n+e) = a(n+e, n) inside every region (Sec. 4
+ * splits a symmetric composite matrix into symmetric region matrices): it keeps the centre and
+ * the (S - 1) / 2 slots after it, and reads a coefficient of the other half at the neighbour
+ * that owns its mirror. Each setup compares every mirrored pair of the FP32 coefficients bit
+ * for bit; the half form is used only when all agree, so that the sweeps compute exactly the
+ * rows of the full form and no result changes. Host int; RMG_ERR_ARG for a level outside the
+ * hierarchy, RMG_ERR_STATE before the first numeric setup. */
+rmg_status rmg_hier_coef_planes(rmg_hier* hier, int level, int* planes);
 /* Coarsest composite matrix restricted to unmasked nodes (dense, row-major, host double
  * [(B*nc)^2], dof cu * B + c) and the composite ids of those nodes (host int64[nc]). Pass NULL
  * to query nc (the number of unmasked composite nodes). */

@@ -51,6 +51,7 @@ void rmg_options_default(rmg_options* o) {
   o->precision = RMG_PREC_FP64;
   o->use_graph = 1;
   o->tile_shape = -1;
+  o->symmetric_storage = 1;
 }
 
 rmg_status rmg_create(rmg_ctx** out, int device, void* stream) {
@@ -319,6 +320,16 @@ rmg_status rmg_hier_tile_shape(rmg_hier* hh, int level, int* tx, int* ty, int* t
   if (level < 0 || level >= h.levels()) return fail(h.layout->ctx, RMG_ERR_ARG, "bad level");
   if (h.shape[level] < 0) { *tx = *ty = *tz = 0; return RMG_OK; }
   tile_shape(h, level, tx, ty, tz);
+  return RMG_OK;
+}
+
+rmg_status rmg_hier_coef_planes(rmg_hier* hh, int level, int* planes) {
+  if (!hh || !planes) return RMG_ERR_ARG;
+  Hier& h = hh->h;
+  if (level < 0 || level >= h.levels()) return fail(h.layout->ctx, RMG_ERR_ARG, "bad level");
+  if (h.kind0 == 0) return fail(h.layout->ctx, RMG_ERR_STATE, "no numeric setup yet");
+  const Level& L = *h.lv[level];
+  *planes = (h.half(level) && h.hsc.half_asym == 0) ? (L.kind + 1) / 2 : L.B * L.B * L.kind;
   return RMG_OK;
 }
 

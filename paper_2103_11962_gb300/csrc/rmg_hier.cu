@@ -17,6 +17,8 @@ Hier::~Hier() {
   for (auto e : probe_ev) if (e) cudaEventDestroy(e);
 }
 
+const int* Hier::half_flag() const { return &sc.get()->half_asym; }
+
 // the mixed-precision dense coarse solve (defined with the coarse factorisation below)
 static int mixed_coarse_solve(Hier& h, cudaStream_t st, int nd, int steps, double* nrm);
 
@@ -296,7 +298,8 @@ struct Exec {
   void stencil(int l, const VT* u, Epi epi) {
     const bool pr = probe && l == 0 && h.probe_ev[0];
     launch_stencil(c(), *h.lv[l], coef(l), u, V(l).y.get(), epi, st, &launches,
-                   pr ? h.probe_ev[0] : nullptr, pr ? h.probe_ev[1] : nullptr, h.sweep(l));
+                   pr ? h.probe_ev[0] : nullptr, pr ? h.probe_ev[1] : nullptr, h.sweep(l),
+                   h.half(l), h.half_flag());
     if (pr) probe = false;
   }
 
@@ -620,6 +623,8 @@ void hier_build(Hier& h) {
   RMG_REQUIRE(o.precision >= 0 && o.precision <= 2, RMG_ERR_ARG, "unknown precision");
   RMG_REQUIRE(o.tile_shape >= -1 && o.tile_shape < kNumTileShapes, RMG_ERR_ARG,
               "tile_shape must be -1 (autotune) or a shape index");
+  RMG_REQUIRE(o.symmetric_storage == 0 || o.symmetric_storage == 1, RMG_ERR_ARG,
+              "symmetric_storage must be 0 or 1");
   RMG_REQUIRE(o.eig_ratio > 1.0 && o.boost > 0.0 && o.power_iters >= 1 &&
               o.power_iters <= 100, RMG_ERR_ARG, "bad Chebyshev options");
   RMG_REQUIRE(o.smoother != RMG_SMOOTHER_GS || h.layout->L0.B == 1, RMG_ERR_ARG,
@@ -654,6 +659,8 @@ void hier_build(Hier& h) {
       if (o.precision == RMG_PREC_FP32_BF16COEF) L.coef16.ensure((size_t)L.B * L.B * L.kind * L.n_r);
     }
   }
+  // half planes for the FP32 cycle's level-0 sweeps of a scalar operator
+  h.half_on = o.symmetric_storage != 0 && o.precision == RMG_PREC_FP32 && h.lv[0]->B == 1;
   if (Lv > 1) h.layout->apbuf.ensure((size_t)(h.lv[0]->dim == 3 ? 27 : 9) * h.lv[0]->n_r);
   h.sc.alloc(1);
   RMG_CUDA(cudaMemsetAsync(h.sc.get(), 0, sizeof(Scalars), c.stream));
@@ -920,12 +927,12 @@ static void power_method_t(Hier& h, int l) {
   VT* b = V.r.get();
   for (int it = 0; it < h.o.power_iters; ++it) {
     launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr, nullptr,
-                   nullptr, h.sweep(l));
+                   nullptr, h.sweep(l), h.half(l), h.half_flag());
     std::swap(a, b);
     if (sizeof(VT) < 8 && (it + 1) % 8 == 0 && it + 1 < h.o.power_iters) normalise(a);
   }
   launch_stencil(c, L, coef, a, V.y.get(), EpiScaled<VT>{dinv, b}, st, nullptr, nullptr,
-                 nullptr, h.sweep(l));
+                 nullptr, h.sweep(l), h.half(l), h.half_flag());
   dot_t<VT>(c, n, L.n_r, a, b, L.mult.get(), &sc->pw_num, FIN_STORE, st);
   dot_t<VT>(c, n, L.n_r, a, a, L.mult.get(), &sc->pw_den, FIN_STORE, st);
   k_cheb_coeffs<<<1, 1, 0, st>>>(sc, l, h.o.eig_ratio, h.o.boost, h.o.cheb_degree);
@@ -1097,6 +1104,20 @@ static void level0_to_fp32(Hier& h) {
   const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
   k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
   RMG_LAUNCHED();
+  if (!h.half_on) return;
+  // the FP32 cycle's half planes and the flag that says whether they hold the operator
+  h.half32.ensure((size_t)(L.kind + 1) / 2 * L.n_r);
+  int* flag = &h.sc.get()->half_asym;
+  RMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
+  const Grid G = L.grid();
+  const int gb = persistent_grid(c, G.ntiles);
+  switch (L.kind) {
+    case 5: k_half_pack<5><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
+    case 7: k_half_pack<7><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
+    case 9: k_half_pack<9><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
+    default: k_half_pack<27><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
+  }
+  RMG_LAUNCHED();
 }
 
 // The mixed cycle's remaining copies: FP32 D~^-1 on every level and, for the BF16 variant, the
@@ -1190,7 +1211,7 @@ static void autotune_t(Hier& h) {
       auto run = [&]() {
         launch_stencil(c, L, ex.coef(l), (const VT*)V.u.get(), V.y.get(),
                        EpiResid<VT>{V.b.get(), V.r.get()}, st, nullptr, nullptr, nullptr,
-                       &h.sgrid[l]);
+                       &h.sgrid[l], h.half(l), h.half_flag());
       };
       run();
       RMG_CUDA(cudaEventRecord(e0, st));

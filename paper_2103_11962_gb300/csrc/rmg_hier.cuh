@@ -78,6 +78,10 @@ struct Hier {
   DBuf<double> x, r, z, p, q, zold, tmp;
   DBuf<float> zold32;                        // previous FP32 cycle output (flexible CG)
   double* pinned = nullptr;                  // host-mapped residual read-back
+  // FP32 cycle, scalar operator: level 0 also as half planes (k_half_pack), read by the sweeps
+  // while the device flag Scalars::half_asym is 0
+  bool half_on = false;
+  DBuf<float> half32;
 
   ~Hier();
   int levels() const { return (int)lv.size(); }
@@ -86,6 +90,9 @@ struct Hier {
     return l < (int)shape.size() && shape[l] >= 0 ? &sgrid[l] : nullptr;
   }
   bool mixed() const { return o.precision != RMG_PREC_FP64; }
+  // half planes of level l for the FP32 sweeps, or null
+  const float* half(int l) const { return (l == 0 && half_on) ? half32.get() : nullptr; }
+  const int* half_flag() const;
 };
 
 void hier_build(Hier& h);          // symbolic: coarse layouts, buffers

@@ -209,6 +209,7 @@ struct Scalars {
   double pw_norm, pw_inv;  // power method scratch (norm and its reciprocal)
   double pw_num, pw_den;
   double rz, pq, alpha, beta, rr, bb, rz_new;
+  int half_asym;           // level-0 FP32 stencil not bitwise symmetric (full planes in use)
 };
 
 struct Ctx {

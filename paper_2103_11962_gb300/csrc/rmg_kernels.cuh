@@ -121,6 +121,113 @@ k_stencil(Grid G, const CT* __restrict__ coef, const VT* __restrict__ u,
   RMG_END_FOR_NODES
 }
 
+// ---- half storage of a symmetric FP32 stencil ----------------------------------------------
+// In every stencil kind slot S-1-s is the mirror offset of slot s and the centre is slot
+// C = (S-1)/2. A symmetric regional operator has a(n, n+e) = a(n+e, n), so planes C..S-1 hold
+// it all: half plane p is slot C+p at every node, and slot s < C of node n is half plane
+// S-1-s-C at the neighbour n + off(s). stencil_row_half forms the same products in the same
+// order as stencil_row, so its row is bit for bit the full form's whenever the mirrored pairs
+// are bitwise equal.
+template <int KIND>
+__host__ __device__ constexpr bool mirrored_slots() {
+  using S = Sten<KIND>;
+  if (2 * S::CENTER + 1 != S::S) return false;
+  for (int s = 0; s < S::S; ++s)
+    if (S::dx(S::S - 1 - s) != -S::dx(s) || S::dy(S::S - 1 - s) != -S::dy(s) ||
+        S::dz(S::S - 1 - s) != -S::dz(s))
+      return false;
+  return true;
+}
+
+template <int KIND>
+__device__ __forceinline__ float stencil_row_half(const float* __restrict__ half,
+                                                  const float* __restrict__ u, int n, int n_r,
+                                                  int i, int j, int l, const RegionDev& R) {
+  using S = Sten<KIND>;
+  static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
+  constexpr int C = S::CENTER;
+  float au = 0.f;
+  const int sy = R.nx, sz = R.nx * R.ny;
+#pragma unroll
+  for (int s = 0; s < S::S; ++s) {
+    const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+    bool ok = true;
+    if (dx < 0) ok &= (i > 0);
+    if (dx > 0) ok &= (i < R.nx - 1);
+    if (dy < 0) ok &= (j > 0);
+    if (dy > 0) ok &= (j < R.ny - 1);
+    if (dz < 0) ok &= (l > 0);
+    if (dz > 0) ok &= (l < R.nz - 1);
+    if (ok) {
+      const int nb = n + dx + dy * sy + dz * sz;
+      const float c = s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
+                            : half[(size_t)(s - C) * (size_t)n_r + n];
+      au = fmaf(c, u[nb], au);
+    }
+  }
+  return au;
+}
+
+// Half planes of a float stencil; *asym becomes 1 when a mirrored pair inside a region differs
+// in any bit (the sweeps then keep reading the full planes).
+template <int KIND>
+__global__ void __launch_bounds__(kTile)
+k_half_pack(Grid G, const float* __restrict__ coef, float* __restrict__ half,
+            int* __restrict__ asym) {
+  using S = Sten<KIND>;
+  static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
+  constexpr int C = S::CENTER;
+  bool bad = false;
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    RMG_DECODE(i, j, l);
+    const int sy = R.nx, sz = R.nx * R.ny;
+#pragma unroll
+    for (int s = C; s < S::S; ++s) {
+      const float cv = coef[(size_t)s * G.n_r + n];
+      half[(size_t)(s - C) * G.n_r + n] = cv;
+      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+      bool ok = s > C;
+      if (dx < 0) ok &= (i > 0);
+      if (dx > 0) ok &= (i < R.nx - 1);
+      if (dy < 0) ok &= (j > 0);
+      if (dy > 0) ok &= (j < R.ny - 1);
+      if (dz < 0) ok &= (l > 0);
+      if (dz > 0) ok &= (l < R.nz - 1);
+      if (ok) {
+        const float mv = coef[(size_t)(S::S - 1 - s) * G.n_r + n + dx + dy * sy + dz * sz];
+        bad |= __float_as_uint(cv) != __float_as_uint(mv);
+      }
+    }
+  RMG_END_FOR_NODES
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *asym = 1;
+}
+
+// Phase A of the FP32 cycle on a level with half planes: the half form when the pack found the
+// operator symmetric (*asym == 0), else the full planes as k_stencil.
+template <bool HALF, int KIND, class Epi>
+__device__ __forceinline__ void stencil_pass(const Grid& G, const float* __restrict__ coef,
+                                             const float* __restrict__ u,
+                                             const uint8_t* __restrict__ mult,
+                                             float* __restrict__ y, const Epi& epi) {
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    RMG_DECODE(i, j, l);
+    const float au = HALF ? stencil_row_half<KIND>(coef, u, n, G.n_r, i, j, l, R)
+                          : stencil_row<KIND, float, float, float>(coef, u, n, G.n_r, i, j, l, R);
+    if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
+  RMG_END_FOR_NODES
+}
+
+template <int KIND, class Epi>
+__global__ void __launch_bounds__(kTile)
+k_stencil_half(Grid G, const float* __restrict__ coef, const float* __restrict__ half,
+               const int* __restrict__ asym, const float* __restrict__ u,
+               const uint8_t* __restrict__ mult, float* __restrict__ y, Epi epi) {
+  if (*asym) stencil_pass<false, KIND>(G, coef, u, mult, y, epi);
+  else stencil_pass<true, KIND>(G, half, u, mult, y, epi);
+}
+
 // Phase B: interface groups. y holds the partial row results of every copy. One thread per
 // copy: it sums the partial results of its group in ascending slot order (every copy of a group
 // forms the identical sum) and applies the epilogue to its own copy.

@@ -2,6 +2,8 @@
 // blocks) and phase B (interface groups) with one epilogue.
 #pragma once
 
+#include <type_traits>
+
 #include "rmg_kernels.cuh"
 
 namespace rmg {
@@ -16,15 +18,33 @@ void launch_groups(Ctx& c, const Level& L, const AT* y, Epi epi, cudaStream_t st
 }
 
 // Phase A over `sweep` (a tuned tile list of L; the level's run tiles when null), then phase B.
+// An FP32 sweep given half planes (see k_half_pack) and their asymmetry flag reads the half
+// form while the flag is 0.
 template <class Epi, typename CT, typename VT, typename AT>
 void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,
                     cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
-                    cudaEvent_t ev1 = nullptr, const Grid* sweep = nullptr) {
+                    cudaEvent_t ev1 = nullptr, const Grid* sweep = nullptr,
+                    const float* half = nullptr, const int* asym = nullptr) {
   const Grid G = sweep ? *sweep : L.grid();
   const int gb = persistent_grid(c, G.ntiles);
   // external record nodes when capturing, so the events can be timed after a graph replay
   if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));
-  if (L.B == 1) {
+  bool done = false;
+  if constexpr (std::is_same<CT, float>::value && std::is_same<VT, float>::value &&
+                std::is_same<AT, float>::value) {
+    if (half && L.B == 1) {
+      RMG_REQUIRE(asym != nullptr, RMG_ERR_STATE, "half planes without their flag");
+      switch (L.kind) {
+        case 5: k_stencil_half<5><<<gb, kTile, 0, st>>>(G, coef, half, asym, u, L.mult.get(), y, epi); break;
+        case 7: k_stencil_half<7><<<gb, kTile, 0, st>>>(G, coef, half, asym, u, L.mult.get(), y, epi); break;
+        case 9: k_stencil_half<9><<<gb, kTile, 0, st>>>(G, coef, half, asym, u, L.mult.get(), y, epi); break;
+        default: k_stencil_half<27><<<gb, kTile, 0, st>>>(G, coef, half, asym, u, L.mult.get(), y, epi); break;
+      }
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (L.B == 1) {
     switch (L.kind) {
       case 5: k_stencil<5, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;
       case 7: k_stencil<7, CT, VT, AT><<<gb, kTile, 0, st>>>(G, coef, u, L.mult.get(), y, epi); break;

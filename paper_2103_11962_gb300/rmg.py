@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("eig_ratio", ctypes.c_double), ("boost", ctypes.c_double),
                 ("power_iters", ctypes.c_int), ("power_seed_base", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("tile_shape", ctypes.c_int)]
+                ("tile_shape", ctypes.c_int), ("symmetric_storage", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
         "rmg_hier_tile_shape": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]),
+        "rmg_hier_coef_planes": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "rmg_hier_coarse_matrix": (ctypes.c_int, [P, I64P, P, P]),
         "rmg_hier_vcycle_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_launch_count": (ctypes.c_ulonglong, []),
@@ -135,7 +136,8 @@ def exported_symbols():
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
             "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
             "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor",
-            "rmg_hier_tile_shape", "rmg_hier_galerkin", "rmg_mlp_num_params", "rmg_mlp_create",
+            "rmg_hier_tile_shape", "rmg_hier_coef_planes", "rmg_hier_galerkin",
+            "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
             "rmg_mlp_train", "rmg_hier_mlp_features", "rmg_hier_mlp_weights"]
 
@@ -319,6 +321,12 @@ class Hierarchy:
         self.ctx.check(lib().rmg_hier_tile_shape(self.h, level, ctypes.byref(a), ctypes.byref(b),
                                                  ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def coef_planes(self, level):
+        """Stencil coefficients per node the cycle's sweeps read on a level (half form: fewer)."""
+        v = ctypes.c_int()
+        self.ctx.check(lib().rmg_hier_coef_planes(self.h, level, ctypes.byref(v)))
+        return v.value
 
     def lam(self, level):
         v = ctypes.c_double()
