@@ -110,6 +110,39 @@ def test_lemma1_split_sums_to_composite(name, request):
     assert abs(lay.Psi @ Ar @ lay.Psi.T - p.A).max() <= 1e-15 * abs(p.A).max() * 4
 
 
+@pytest.mark.parametrize("name", ["p2d", "p3d", "q3d"])
+def test_split_of_a_symmetric_matrix_is_symmetric(name, request):
+    """Sec. 4 divides A_ij and A_ji by the same count q_ij = q_ji (the regions holding both
+    nodes), so a symmetric A gives region matrices that are symmetric bit for bit. This is
+    what lets the FP32 cycle store half of a region stencil. A single moved entry breaks
+    exactly the mirrored pairs that hold it."""
+    p = request.getfixturevalue(name)
+    A = p.A.tocsr()
+    assert (A - A.T).count_nonzero() == 0
+    lay = make_layout(p.region_dims, p.region_gids, p.n_nodes, p.dirichlet)
+    Ar = split_regional(lay, A).tocsr()
+    assert (Ar - Ar.T).count_nonzero() == 0
+    # the same after rounding to FP32, where the half form compares the pairs
+    A32 = Ar.astype(np.float32)
+    assert (A32 - A32.T).count_nonzero() == 0
+    # move one off-diagonal entry between two free nodes: every copy of that edge in the
+    # regional matrix loses its mirror
+    free = ~p.dirichlet.astype(bool)
+    rows, cols = A.nonzero()
+    k = next(t for t in range(len(rows))
+             if rows[t] < cols[t] and free[rows[t]] and free[cols[t]])
+    i, j = int(rows[k]), int(cols[k])
+    B = A.copy()
+    B[i, j] = B[i, j] * (1.0 + 2.0 ** -10)
+    Br = split_regional(lay, B).tocsr()
+    D = (Br - Br.T).tocsr()
+    D.eliminate_zeros()
+    # q_ij copies of the edge, each a pair (a, b) and (b, a) in the difference
+    q = sum(1 for r in range(lay.m)
+            if {i, j} <= set(int(g) for g in lay.region_gids[lay.offsets[r]:lay.offsets[r + 1]]))
+    assert q >= 1 and D.nnz == 2 * q
+
+
 def test_split_entries_follow_rule(p3d):
     """Off-diagonals are A_ij / q_ij; interior region rows (away from masks) sum to zero."""
     lay = make_layout(p3d.region_dims, p3d.region_gids, p3d.n_nodes, p3d.dirichlet)
