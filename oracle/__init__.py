@@ -22,9 +22,7 @@ Parity status of every function is pinned by ``tests/test_oracle_*.py`` against 
 lemmas of the paper and brute force; the exceptions are listed in ``UNPINNED``.
 """
 
-UNPINNED = {
-    # The power-method start vector and iteration count are the oracle's reading; the paper
-    # only says "a few iterations of the power method" with random vectors. The estimate is
-    # pinned to lie below the true maximum and near it, not to a printed value.
-    "smoothers.power_method": "partially pinned (bounds only)",
-}
+# Every function is pinned. The power method is pinned to its closed form in the eigenpairs of
+# D^-1/2 A D^-1/2 and to the bounds (0.85 lambda_max, lambda_max]. Its start vector and step
+# count are readings (the paper leaves both open), not pins.
+UNPINNED = {}

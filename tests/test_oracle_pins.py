@@ -428,6 +428,26 @@ def test_power_method_bounds():
     assert cm.levels[0].lam == pytest.approx(lam, rel=1e-12)
 
 
+@pytest.mark.parametrize("k", [1, 3, 10])
+def test_power_method_equals_its_spectral_closed_form(k):
+    """k normalised power steps on M = D^-1 A, then x^T M x / x^T x, written out through the
+    eigenpairs of the symmetric S = D^-1/2 A D^-1/2 = Q L Q^T (M = D^-1/2 S D^1/2). With
+    c = Q^T D^1/2 x0, M^k x0 = D^-1/2 Q L^k c, so the estimate is
+    (L^k c)^T Q^T D^-1 Q (L^(k+1) c) / (L^k c)^T Q^T D^-1 Q (L^k c), with no iteration.
+    A dropped D^-1, a step too many or too few, or another quotient fails."""
+    p = W.diffusion3d_7pt(region_grid=(1, 1, 1), choices=(10,), seed=3)
+    A = p.A.toarray()
+    d = np.diag(A).copy()
+    x0 = uniform_pm1(10, np.arange(p.n_nodes))
+    x0[p.dirichlet.astype(bool)] = 0.0
+    lam = smoothers.power_method(lambda v: p.A @ v, 1.0 / d, np.dot, x0, iters=k)
+    L, Q = np.linalg.eigh(A / np.sqrt(np.outer(d, d)))
+    c = Q.T @ (np.sqrt(d) * x0)
+    G = Q.T @ (Q / d[:, None])                  # Q^T D^-1 Q
+    a, b = L ** k * c, L ** (k + 1) * c
+    assert lam == pytest.approx((a @ G @ b) / (a @ G @ a), rel=1e-12)
+
+
 # ---------------------------------------------------------------------------- cycles
 @pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
 @pytest.mark.parametrize("name", ["p2d", "p3d"])
