@@ -35,8 +35,8 @@ METRIC = "V-cycle DOF/s & time to 1e-10 rel. residual, mixed/learned vs plain FP
 RTOL = 1e-10
 
 # Per-node algorithmic bytes and FP64 flops of the timed kernel, the fine-level Chebyshev
-# recurrence sweep with a 7-point stencil (k_stencil<7, EpiCheb>): 7 coefficients, u, b,
-# D~^-1, d read; d and u_out written; 1-byte multiplicity read.
+# recurrence sweep (k_stencil_half, k_stencil or k_bstencil with EpiCheb): its coefficient
+# streams, u, b, D~^-1, d read; d and u_out written; 1-byte multiplicity read.
 def sweep_bytes(prec, planes, B=1):
     """Algorithmic bytes per regional node of the Chebyshev recurrence sweep: the stencil
     coefficients the sweep reads per node (`planes`: B*B*S, or (S+1)/2 for the half form of a
