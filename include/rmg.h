@@ -175,6 +175,21 @@ rmg_status rmg_operator_from_block_csr(rmg_layout* layout, int stencil, int dofs
                                        const int64_t* rowptr, const int64_t* col,
                                        const double* val);
 
+/* The same split as rmg_operator_from_csr (dofs_per_node = 1) or rmg_operator_from_block_csr
+ * (dofs_per_node = 3), from a composite CSR in HOST memory, the form in which an application
+ * usually holds its assembled matrix (Sec. 4: the application supplies the composite operator
+ * and the region map, and the library dis-assembles it). rowptr is host int64[n_rows + 1] with
+ * n_rows = n_composite * dofs_per_node and rowptr[0] = 0; col (host int64) and val (host
+ * double) have rowptr[n_rows] entries. The arrays are copied to device buffers that the layout
+ * owns (allocated on the first call, reallocated only when nnz changes, freed with the layout),
+ * with cudaMemcpyAsync on the context's stream; page-locked host arrays make these copies DMA
+ * transfers. The host arrays may be reused once the call returns. Errors: RMG_ERR_ARG for null
+ * pointers, dofs_per_node other than 1 or 3, or a rowptr that does not start at 0; otherwise
+ * those of the device-CSR calls. Synchronises the stream. */
+rmg_status rmg_operator_from_host_csr(rmg_layout* layout, int stencil, int dofs_per_node,
+                                      const int64_t* rowptr, const int64_t* col,
+                                      const double* val);
+
 /* Set already-split region matrices directly: coeffs is device double[stencil * n_r],
  * slot-major (coefficient s of regional node n at s * n_r + n). Slot order: 7-point
  * (-z,-y,-x,0,+x,+y,+z); 5-point (-y,-x,0,+x,+y); 9/27-point: (dx+1) + 3(dy+1) [+ 9(dz+1)]. */
@@ -211,7 +226,7 @@ void rmg_hier_destroy(rmg_hier* hier);
 /*
  * Interpolation with stored per-node weights (the general transfers of Table 4 "Generic": the
  * sparsity of 3:1 linear interpolation, coefficients of the caller's choice). wr is device
- * double[3 * n_r(level)], axis-major: wr[a * n_r + n] is the weight regional fine node n takes
+ * float[3 * n_r(level)], axis-major: wr[a * n_r + n] is the weight regional fine node n takes
  * from its right coarse neighbour along axis a (1 - wr from the left one); it is ignored along
  * axes where n sits on a coarse index. Co-located copies must carry identical weights and
  * interface nodes may only use interface coarse nodes (Lemma 2); weights computed from
@@ -276,17 +291,31 @@ rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, float* 
 rmg_status rmg_hier_convergence_factor(rmg_hier* hier, int iters, unsigned long long seed,
                                        double* factor);
 
-/* One V-cycle with zero initial guess: z = M^-1 r. r and z are device vectors, composite
- * (layout_flag = 0) or regional and consistent (layout_flag = 1). */
+/* One regional V-cycle with zero initial guess, z = M^-1 r: the regional mgCycle of the
+ * figure in Sec. 3.6 with the operations of Sec. 3.3 (smoothing with the regional residual,
+ * restriction w = Psibar^T Psibar [[R]] [[Psi Psi^T]]^-1 r, recursion, coarse solve of the
+ * composite coarsest operator, Sec. 3.5, region-local prolongation, post-smoothing). r and z
+ * are device vectors, composite (layout_flag = 0) or regional and consistent
+ * (layout_flag = 1). A composite r is copied into every regional copy; the regional output is
+ * returned as the mean over the copies (the composite value). Errors: RMG_ERR_STATE when the
+ * coarsest level exceeds the dense solver (RMG_MAX_DENSE). Returns once queued. */
 rmg_status rmg_vcycle_apply(rmg_hier* hier, const double* r, double* z, int layout_flag);
 
 /*
- * Preconditioned conjugate gradients in FP64 with one V-cycle as preconditioner. b and x
- * are device composite vectors (x: in = initial guess, out = solution). Entries at masked
- * nodes of b are taken as zero. Stops when ||r||_2 / ||b||_2 <= rtol on the recurrence
- * residual, or after maxit iterations (RMG_ERR_NOT_CONVERGED, x still written).
- * history: host double[maxit + 1] or NULL, receives the relative residual per iteration.
- * Synchronises the stream once per iteration (the convergence test).
+ * Preconditioned conjugate gradients in FP64 with one V-cycle as preconditioner (Sec. 6.2
+ * notes that the region multigrid is normally used as a Krylov preconditioner; the paper's
+ * runs use it as a stand-alone solver). b and x are device composite vectors (x: in =
+ * initial guess, out = solution). Entries at masked nodes of b are taken as zero. The plain
+ * method (RMG_PREC_FP64) runs textbook PCG; the FP32 and BF16 cycles and the region
+ * Gauss-Seidel cycle run inside flexible CG (beta = r.(z - z_old) / r_old.z_old). Every inner
+ * product, update and the stopping test are FP64; the FP32 cycle receives the residual scaled
+ * by a power of two near 1/||b|| (exact, and the cycle is linear), so the result does not
+ * depend on the scale of b. When the recurrence residual passes ||r||_2 / ||b||_2 <= rtol the
+ * true residual b - A x is recomputed in FP64; the solve stops only if that one passes too,
+ * and otherwise restarts from the true residual. It returns RMG_ERR_NOT_CONVERGED (x still
+ * written) after maxit iterations. history: host double[maxit + 1] or NULL, receives the
+ * relative residual per iteration. Synchronises the stream once per iteration (the
+ * convergence test).
  */
 rmg_status rmg_pcg_solve(rmg_hier* hier, const double* b, double* x, double rtol, int maxit,
                          double* history, rmg_solve_info* info);
@@ -310,9 +339,12 @@ rmg_status rmg_pcg_solve(rmg_hier* hier, const double* b, double* x, double rtol
  * library until the process exits, with room for at most 4096 regions and 4,194,304
  * composite nodes; larger inputs fail with RMG_ERR_ARG before any work is queued. Each call
  * rewrites the region table and zeroes the accumulator it keeps there; calls that overlap
- * on the GPU (other streams or host threads) share the array and race. The first call on a
- * device takes the device address of the array (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. The summation order over the
+ * on the GPU (other streams or host threads) share the array and race. The work runs on the
+ * device that cuda_stream belongs to (the current device for the legacy default stream): the
+ * call makes that device current for its duration and restores the caller's device before
+ * it returns. The first call for a device takes the device address of that device's copy of
+ * the array (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. The summation order over the
  * copies of an interface node is not fixed (atomic adds), so results can differ from
  * rmg_regional_apply in the last bits. Regional nodes whose gid is outside
  * [0, n_composite) receive NaN. Returns once the work is queued.

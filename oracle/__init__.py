@@ -16,7 +16,8 @@ paper's formulas to them, so each step can be checked against the text by eye:
 * ``cycle``     - the composite V-cycle and the regional V-cycle (Sec. 3.3, Sec. 3.6 figure).
 * ``krylov``    - preconditioned conjugate gradients (the paper only mentions Krylov use).
 * ``rng``       - SplitMix64 as a counter-based generator (for power-method start vectors).
-* ``local``     - per-node evaluations used to spot-check full-size GPU runs.
+* ``learned``   - operator-dependent weights, the learned prolongator's features and its small
+                  MLP (forward, loss and gradient); no paper basis, pinned by closed forms.
 
 Parity status of every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 lemmas of the paper and brute force; the exceptions are listed in ``UNPINNED``.

@@ -13,6 +13,15 @@ operator-dependent candidate below, computed from the composite matrix:
 The MLP functions are a plain FP64 restatement of the network (27 features padded to 32 ->
 64 -> 64 -> 3, ReLU, ReLU, sigmoid) with the BF16 roundings of the GPU forward pass applied
 at the same points, used to check the GPU gradients.
+
+The network input (``features``) is, per fine node and axis, the line of three edges between
+its two coarse neighbours read from the composite matrix: log10 of the three conductances
+-A(p_e, p_e+1) and of the four diagonals A(p_i, p_i), each divided by the node's own
+diagonal, then rem/3 and an active flag (zero along axes where the node sits on a coarse
+index). Its output (``weights_from_outputs``) is the right-neighbour weight per active axis.
+The paper has no learned transfer: the network, its features and its outputs are readings
+of the scope, pinned by closed forms (a hand-set network, the constant-coefficient
+Laplacian's features) rather than by the paper.
 """
 from __future__ import annotations
 
@@ -122,3 +131,49 @@ def loss_and_grad(params, X, Y, M, rounding=True):
     db1 = dZ1.sum(axis=0)
     grad = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
     return L, grad
+
+
+# ------------------------------------------------------------------------------ features
+def features(A: sp.csr_matrix, global_dims) -> np.ndarray:
+    """(n, 32) network inputs of every composite node (columns 27..31 are zero padding).
+
+    Per axis a (9 columns from 9a): a node at remainder rem = c_a mod 3 != 0 lies between the
+    coarse nodes p_0 = g - rem s_a and p_3 = p_0 + 3 s_a. With d_g = A(g, g) (1 when not
+    positive): log10(max(k_e / d_g, 1e-12)) capped at 2 for the conductances
+    k_e = -A(p_e, p_e + s_a), e = 0, 1, 2; log10(max(A(p_i, p_i) / d_g, 1e-12)) capped at 12
+    for i = 0..3; rem / 3; 1. An axis with rem = 0, or one the grid does not have (2D: z), is
+    all zero."""
+    Nx, Ny, Nz = global_dims
+    n = Nx * Ny * Nz
+    A = sp.csr_matrix(A)
+    diag = A.diagonal()
+    g = np.arange(n)
+    coord = [g % Nx, (g // Nx) % Ny, g // (Nx * Ny)]
+    stride = [1, Nx, Nx * Ny]
+    dims = [Nx, Ny, Nz]
+    dref = np.where(diag > 0, diag, 1.0)
+    F = np.zeros((n, NFEAT))
+    for a in range(3):
+        if dims[a] == 1:
+            continue
+        rem = coord[a] % 3
+        act = np.flatnonzero(rem != 0)
+        r = rem[act]
+        p0 = act - r * stride[a]
+        for e in range(3):
+            i = p0 + e * stride[a]
+            k = -np.asarray(A[i, i + stride[a]]).ravel()
+            F[act, 9 * a + e] = np.minimum(np.log10(np.maximum(k / dref[act], 1e-12)), 2.0)
+        for e in range(4):
+            d = diag[p0 + e * stride[a]]
+            F[act, 9 * a + 3 + e] = np.minimum(np.log10(np.maximum(d / dref[act], 1e-12)), 12.0)
+        F[act, 9 * a + 7] = r / 3.0
+        F[act, 9 * a + 8] = 1.0
+    return F
+
+
+def weights_from_outputs(feats, out) -> np.ndarray:
+    """(3, n) right-neighbour weights: the network output along active axes, 0 elsewhere."""
+    F = np.asarray(feats)
+    O = np.asarray(out)
+    return np.stack([np.where(F[:, 9 * a + 8] > 0.5, O[:, a], 0.0) for a in range(3)])

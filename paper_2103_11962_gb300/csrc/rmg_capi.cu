@@ -1,4 +1,5 @@
 // extern "C" entry points: argument checks, exception -> status translation.
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -136,6 +137,37 @@ rmg_status rmg_operator_from_block_csr(rmg_layout* lay, int stencil, int dofs_pe
   if (!lay) return RMG_ERR_ARG;
   return guarded(lay->ctx, [&] {
     split_from_csr(lay->ctx->c, lay->L0, stencil, dofs_per_node, rowptr, col, val);
+    lay->ybuf.ensure((size_t)dofs_per_node * lay->L0.n_r);
+    lay->has_operator = true;
+  });
+}
+
+rmg_status rmg_operator_from_host_csr(rmg_layout* lay, int stencil, int dofs_per_node,
+                                      const int64_t* rowptr, const int64_t* col,
+                                      const double* val) {
+  if (!lay) return RMG_ERR_ARG;
+  return guarded(lay->ctx, [&] {
+    RMG_REQUIRE(rowptr && col && val, RMG_ERR_ARG, "null CSR array");
+    RMG_REQUIRE(dofs_per_node == 1 || dofs_per_node == 3, RMG_ERR_ARG,
+                "dofs_per_node must be 1 or 3");
+    const size_t nrows = (size_t)lay->L0.ncomp * (size_t)dofs_per_node;
+    RMG_REQUIRE(rowptr[0] == 0 && rowptr[nrows] >= 0, RMG_ERR_ARG,
+                "rowptr must start at 0 and end at nnz >= 0");
+    const size_t nnz = (size_t)rowptr[nrows];
+    cudaStream_t st = lay->ctx->c.stream;
+    lay->csr_rowptr.ensure(nrows + 1);
+    lay->csr_col.ensure(std::max<size_t>(nnz, 1));
+    lay->csr_val.ensure(std::max<size_t>(nnz, 1));
+    RMG_CUDA(cudaMemcpyAsync(lay->csr_rowptr.get(), rowptr, (nrows + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, st));
+    if (nnz) {
+      RMG_CUDA(cudaMemcpyAsync(lay->csr_col.get(), col, nnz * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, st));
+      RMG_CUDA(cudaMemcpyAsync(lay->csr_val.get(), val, nnz * sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+    }
+    split_from_csr(lay->ctx->c, lay->L0, stencil, dofs_per_node, lay->csr_rowptr.get(),
+                   lay->csr_col.get(), lay->csr_val.get());
     lay->ybuf.ensure((size_t)dofs_per_node * lay->L0.n_r);
     lay->has_operator = true;
   });

@@ -172,84 +172,96 @@ k_cg_update(int n, int n_nodes, const double* __restrict__ p, const double* __re
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// Mixed-precision cycle. GB300 retires two FP64 instructions per clock per SM (conversions
-// between FP32 and FP64 included), so the vector kernels around the FP32 cycle keep FP64 only
-// where the solution depends on it: x, r and p are FP64 and updated in FP64; the inner products
-// that only steer the flexible iteration (r.r for the stopping test, r.z and r.z_old for alpha
-// and beta) multiply the FP32 copy of r with the FP32 cycle output and add runs of 16 products
-// in FP32 into FP64 accumulators.
-constexpr int kRun = 16;
+// Mixed-precision cycle. The FP32 (or BF16-coefficient) V-cycle is the preconditioner of a
+// flexible CG that keeps x, r and p in FP64 and forms every inner product in FP64: r.r for the
+// stopping test, r.z and r.z_old for alpha and beta. The cycle's right-hand side is the FP64
+// residual times rscale = 2^-e, a power of two near 1/||b||, rounded to FP32: the scaling is
+// exact and the cycle is linear, so its output is z / rscale and the iteration does not depend
+// on the scale of b (without it, residual entries below ~1e-19 or above ~1e19 would underflow
+// or overflow in FP32 squares and products). zscale = 1 / rscale undoes it (exactly).
 
-// x += alpha p, r -= alpha q (FP64); r32 = FP32 copy of the new r (the cycle's right-hand
-// side); partial sums of r.r from r32.
+// x += alpha p, r -= alpha q (FP64); r32 = FP32(r * rscale), the cycle's right-hand side;
+// partial sums of r.r / mult in FP64.
 __global__ void __launch_bounds__(256)
 k_cg_update_mixed(int n, int n_nodes, const double* __restrict__ p, const double* __restrict__ q,
                   const uint8_t* __restrict__ mult, const Scalars* __restrict__ sc,
-                  double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
-                  double* __restrict__ partials) {
+                  double rscale, double* __restrict__ x, double* __restrict__ r,
+                  float* __restrict__ r32, double* __restrict__ partials) {
   const double a = sc->alpha;
   double s = 0.0;
-  float run = 0.f;
-  int cnt = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     x[k] = fma(a, p[k], x[k]);
     const double rk = fma(-a, q[k], r[k]);
     r[k] = rk;
-    const float rf = (float)rk;
-    r32[k] = rf;
-    run = fmaf(rf * inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]), rf, run);
-    if (++cnt == kRun) { s += (double)run; run = 0.f; cnt = 0; }
+    r32[k] = (float)(rk * rscale);
+    s = fma(rk * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]), rk, s);
   }
-  s += (double)run;
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// Partial sums of r.z and r.z_old from the FP32 residual copy and the FP32 cycle output, which
-// then becomes z_old. Partials of r.z go to partials[0, gridDim), those of r.z_old to
-// partials[gridDim, 2 gridDim). Four consecutive entries per thread step (16-byte loads) keep
-// enough bytes in flight; the entries past the last multiple of four take a scalar tail.
-__device__ __forceinline__ void flex_term(float rk, float im, float zk, float zo, float& run0,
-                                          float& run1) {
-  const float r = rk * im;
-  run0 = fmaf(r, zk, run0);
-  run1 = fmaf(r, zo, run1);
+// r32 = FP32(r * rscale): the cycle's right-hand side at a (re)start of the iteration.
+__global__ void k_to_f32_scaled(int n, const double* __restrict__ r, double rscale,
+                                float* __restrict__ r32) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    r32[k] = (float)(r[k] * rscale);
 }
 
+// Partial sums of r.z and r.z_old in FP64 (the FP32 values convert exactly), times zscale;
+// the FP32 cycle output z then becomes z_old. Partials of r.z go to partials[0, gridDim), those
+// of r.z_old to partials[gridDim, 2 gridDim). Four consecutive FP32 entries per thread step
+// (16-byte loads); the entries past the last multiple of four take a scalar tail.
 __global__ void __launch_bounds__(256)
-k_flex_dots(int n, int n_nodes, const float* __restrict__ r32, const float* __restrict__ z,
-            float* __restrict__ zold, const uint8_t* __restrict__ mult,
+k_flex_dots(int n, int n_nodes, const double* __restrict__ r, const float* __restrict__ z,
+            float* __restrict__ zold, const uint8_t* __restrict__ mult, double zscale,
             double* __restrict__ partials) {
   double s0 = 0.0, s1 = 0.0;
-  float run0 = 0.f, run1 = 0.f;
   const int n4 = n >> 2;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  auto im_of = [&](int k) { return inv_mult<float>(mult[k < n_nodes ? k : k % n_nodes]); };
-  int cnt = 0;
+  auto im_of = [&](int k) { return inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]); };
+  auto term = [&](int k, float zk, float ok) {
+    const double rk = r[k] * im_of(k);
+    s0 = fma(rk, (double)zk, s0);
+    s1 = fma(rk, (double)ok, s1);
+  };
   for (int q = tid; q < n4; q += nth) {
-    const float4 rv = reinterpret_cast<const float4*>(r32)[q];
     const float4 zv = reinterpret_cast<const float4*>(z)[q];
     const float4 ov = reinterpret_cast<const float4*>(zold)[q];
     const int k = 4 * q;
-    flex_term(rv.x, im_of(k), zv.x, ov.x, run0, run1);
-    flex_term(rv.y, im_of(k + 1), zv.y, ov.y, run0, run1);
-    flex_term(rv.z, im_of(k + 2), zv.z, ov.z, run0, run1);
-    flex_term(rv.w, im_of(k + 3), zv.w, ov.w, run0, run1);
+    term(k, zv.x, ov.x);
+    term(k + 1, zv.y, ov.y);
+    term(k + 2, zv.z, ov.z);
+    term(k + 3, zv.w, ov.w);
     reinterpret_cast<float4*>(zold)[q] = zv;
-    if (++cnt == 4) { s0 += (double)run0; s1 += (double)run1; run0 = run1 = 0.f; cnt = 0; }
   }
   for (int k = 4 * n4 + tid; k < n; k += nth) {
-    flex_term(r32[k], im_of(k), z[k], zold[k], run0, run1);
+    term(k, z[k], zold[k]);
     zold[k] = z[k];
   }
-  s0 += (double)run0;
-  s1 += (double)run1;
-  s0 = block_sum<256>(s0);
-  s1 = block_sum<256>(s1);
+  s0 = block_sum<256>(s0 * zscale);
+  s1 = block_sum<256>(s1 * zscale);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = s0;
     partials[gridDim.x + blockIdx.x] = s1;
   }
+}
+
+// First direction after a (re)start: partial sums of r.z in FP64, p = z * zscale (FP64),
+// z_old = z.
+__global__ void __launch_bounds__(256)
+k_start_dir(int n, int n_nodes, const double* __restrict__ r, const float* __restrict__ z,
+            const uint8_t* __restrict__ mult, double zscale, double* __restrict__ p,
+            float* __restrict__ zold, double* __restrict__ partials) {
+  double s = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const float zk = z[k];
+    const double zd = (double)zk * zscale;
+    s = fma(r[k] * inv_mult<double>(mult[k < n_nodes ? k : k % n_nodes]), zd, s);
+    p[k] = zd;
+    zold[k] = zk;
+  }
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void k_axpy_neg(int n, const double* __restrict__ z, double* __restrict__ e) {
@@ -257,12 +269,13 @@ __global__ void k_axpy_neg(int n, const double* __restrict__ z, double* __restri
     e[k] -= z[k];
 }
 
+// p = z * zscale + beta p (zscale = 1 for the FP64 cycle).
 template <typename ZT>
-__global__ void k_p_update(int n, const ZT* __restrict__ z, const Scalars* __restrict__ sc,
-                           double* __restrict__ p) {
+__global__ void k_p_update(int n, const ZT* __restrict__ z, double zscale,
+                           const Scalars* __restrict__ sc, double* __restrict__ p) {
   const double b = sc->beta;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    p[k] = double(z[k]) + b * p[k];
+    p[k] = fma(double(z[k]), zscale, b * p[k]);
 }
 
 // Composite inner product of consistent regional vectors with n entries (B components of
@@ -1396,6 +1409,10 @@ double convergence_factor(Hier& h, int iters, unsigned long long seed) {
 }
 
 // ---------------------------------------------------------------------- PCG
+// Textbook PCG for the plain FP64 cycle, flexible CG (Polak-Ribiere beta) for the FP32/BF16
+// cycles and for the region Gauss-Seidel cycle; every inner product and update in FP64. When
+// the recurrence residual passes the tolerance the true residual b - A x is recomputed; the
+// solve ends only if it passes too, otherwise the iteration restarts from the true residual.
 void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, double* history,
                rmg_solve_info* info) {
   require_dense(h);
@@ -1415,11 +1432,6 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
   const auto t0 = std::chrono::steady_clock::now();
   comp_to_reg(c, L0, b, breg, true);
   comp_to_reg(c, L0, xout, h.x.get(), true);
-  // r = b - A x
-  launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
-                 EpiResid<double>{breg, rvec}, st, nullptr);
-  dot(c, n, L0.n_r, breg, breg, L0.mult.get(), &sc->bb, FIN_STORE, st);
-  dot(c, n, L0.n_r, rvec, rvec, L0.mult.get(), &sc->rr, FIN_STORE, st);
   auto read2 = [&](double* a, double* bb) {
     RMG_CUDA(cudaMemcpyAsync(h.pinned, &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
     RMG_CUDA(cudaMemcpyAsync(h.pinned + 1, &sc->bb, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1428,35 +1440,43 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
     *a = h.pinned[0];
     *bb = h.pinned[1];
   };
+  // out = b - A x and its squared composite norm into sc->rr
+  auto true_residual = [&](double* out) {
+    launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
+                   EpiResid<double>{breg, out}, st, nullptr);
+    dot(c, n, L0.n_r, out, out, L0.mult.get(), &sc->rr, FIN_STORE, st);
+  };
+  true_residual(rvec);
+  dot(c, n, L0.n_r, breg, breg, L0.mult.get(), &sc->bb, FIN_STORE, st);
   double rr = 0, bb = 0;
   read2(&rr, &bb);
   const double bnorm = std::sqrt(bb);
   double relres = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
+  double rtrue = relres;
   if (history) history[0] = relres;
+  // the FP32 cycle's input scaling: a power of two near 1 / ||b|| (exact both ways)
+  const int eb = (bnorm > 0 && std::isfinite(bnorm)) ? std::ilogb(bnorm) : 0;
+  const double rscale = std::ldexp(1.0, -eb), zscale = std::ldexp(1.0, eb);
   int it = 0, ncyc = 0;
   // The FP32 cycle reads its right-hand side from r32 and leaves z32; in the loop, r32 is
   // written by the CG update and z32 is read directly by the dots and the direction update
-  // (the cycle does not modify its level-0 right-hand side, so r32 stays valid for the dots).
+  // (the cycle does not modify its level-0 right-hand side).
   float* r32 = mixed ? h.v32[0].b.get() : nullptr;
   const float* z32 = mixed ? h.v32[0].u.get() : nullptr;
-  int status_conv = 0;
-  if (relres > rtol && bnorm > 0) {
+  bool converged = !(relres > rtol) || !(bnorm > 0);
+  while (!converged && it < maxit) {
+    // (re)start: z = M^-1 r, p = z
     if (mixed) {
-      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, rvec, r32);
+      k_to_f32_scaled<<<eg, 256, 0, st>>>(n, rvec, rscale, r32);
       RMG_LAUNCHED();
     }
     vcycle(h);
     ++ncyc;
     if (mixed) {
-      const int g = std::min(c.max_partials, persistent_grid(c, (n + 255) / 256));
-      k_dot<double, float><<<g, 256, 0, st>>>(n, L0.n_r, rvec, z32, L0.mult.get(),
-                                               c.partials.get());
+      k_start_dir<<<dg, 256, 0, st>>>(n, L0.n_r, rvec, z32, L0.mult.get(), zscale, h.p.get(),
+                                      h.zold32.get(), c.partials.get());
       RMG_LAUNCHED();
-      k_finalize<<<1, 256, 0, st>>>(c.partials.get(), g, &sc->rz, FIN_STORE);
-      RMG_LAUNCHED();
-      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, z32, h.p.get());
-      RMG_LAUNCHED();
-      k_copy<float><<<eg, 256, 0, st>>>(n, z32, h.zold32.get());
+      k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rz, FIN_STORE);
       RMG_LAUNCHED();
     } else {
       dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz, FIN_STORE, st);
@@ -1467,7 +1487,8 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
         RMG_LAUNCHED();
       }
     }
-    for (it = 1; it <= maxit; ++it) {
+    while (it < maxit) {
+      ++it;
       launch_stencil(c, L0, L0.coef.get(), h.p.get(), h.v64[0].y.get(),
                      EpiStore<double>{h.q.get()}, st, nullptr);
       dot(c, n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), &sc->pq, FIN_STORE, st);
@@ -1475,7 +1496,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       RMG_LAUNCHED();
       if (mixed)
         k_cg_update_mixed<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc,
-                                              h.x.get(), rvec, r32, c.partials.get());
+                                              rscale, h.x.get(), rvec, r32, c.partials.get());
       else
         k_cg_update<<<dg, 256, 0, st>>>(n, L0.n_r, h.p.get(), h.q.get(), L0.mult.get(), sc,
                                         h.x.get(), rvec, c.partials.get());
@@ -1485,12 +1506,27 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
       read2(&rr, &bb);
       relres = std::sqrt(rr) / bnorm;
       if (history) history[it] = relres;
-      if (relres <= rtol) { status_conv = 1; break; }
+      if (relres <= rtol) {
+        // confirm on the true residual; q is free until the next product
+        true_residual(h.q.get());
+        double rt = 0;
+        read2(&rt, &bb);
+        rtrue = std::sqrt(rt) / bnorm;
+        if (rtrue <= rtol) {
+          converged = true;
+        } else {
+          // the recurrence drifted from b - A x: restart from the true residual
+          RMG_CUDA(cudaMemcpyAsync(rvec, h.q.get(), (size_t)n * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+          relres = rtrue;
+        }
+        break;
+      }
       vcycle(h);
       ++ncyc;
       if (mixed) {
-        k_flex_dots<<<dg, 256, 0, st>>>(n, L0.n_r, r32, z32, h.zold32.get(), L0.mult.get(),
-                                        c.partials.get());
+        k_flex_dots<<<dg, 256, 0, st>>>(n, L0.n_r, rvec, z32, h.zold32.get(), L0.mult.get(),
+                                        zscale, c.partials.get());
         RMG_LAUNCHED();
         k_finalize<<<1, 256, 0, st>>>(c.partials.get(), dg, &sc->rz_new, FIN_STORE);
         RMG_LAUNCHED();
@@ -1498,7 +1534,7 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
         RMG_LAUNCHED();
         k_beta<<<1, 1, 0, st>>>(sc, 1);
         RMG_LAUNCHED();
-        k_p_update<float><<<eg, 256, 0, st>>>(n, z32, sc, h.p.get());
+        k_p_update<float><<<eg, 256, 0, st>>>(n, z32, zscale, sc, h.p.get());
         RMG_LAUNCHED();
       } else {
         dot(c, n, L0.n_r, rvec, zvec, L0.mult.get(), &sc->rz_new, FIN_STORE, st);
@@ -1509,30 +1545,30 @@ void pcg_solve(Hier& h, const double* b, double* xout, double rtol, int maxit, d
         }
         k_beta<<<1, 1, 0, st>>>(sc, flex64 ? 1 : 0);
         RMG_LAUNCHED();
-        k_p_update<double><<<eg, 256, 0, st>>>(n, zvec, sc, h.p.get());
+        k_p_update<double><<<eg, 256, 0, st>>>(n, zvec, 1.0, sc, h.p.get());
         RMG_LAUNCHED();
       }
     }
-    if (it > maxit) it = maxit;
-  } else {
-    status_conv = 1;
   }
   reg_to_comp(c, L0, h.x.get(), xout, 1);
-  // true residual from the final iterate
-  launch_stencil(c, L0, L0.coef.get(), h.x.get(), h.v64[0].y.get(),
-                 EpiResid<double>{breg, h.q.get()}, st, nullptr);
-  dot(c, n, L0.n_r, h.q.get(), h.q.get(), L0.mult.get(), &sc->rr, FIN_STORE, st);
-  double rtrue = 0;
-  read2(&rtrue, &bb);
+  if (!converged || it == 0) {
+    // true residual of the returned iterate (already known after a confirmed convergence)
+    true_residual(h.q.get());
+    double rt = 0;
+    read2(&rt, &bb);
+    rtrue = bnorm > 0 ? std::sqrt(rt) / bnorm : 0.0;
+  } else {
+    RMG_CUDA(cudaStreamSynchronize(st));
+  }
   const auto t1 = std::chrono::steady_clock::now();
   if (info) {
     info->iterations = it;
     info->relres = relres;
-    info->true_relres = bnorm > 0 ? std::sqrt(rtrue) / bnorm : 0.0;
+    info->true_relres = rtrue;
     info->seconds = std::chrono::duration<double>(t1 - t0).count();
     info->vcycles = ncyc;
   }
-  if (!status_conv)
+  if (!converged)
     throw Error(RMG_ERR_NOT_CONVERGED, "PCG reached maxit with relres " + std::to_string(relres));
 }
 

@@ -243,4 +243,7 @@ struct rmg_layout {
   rmg::DBuf<double> ybuf;         // interface partials for rmg_regional_apply
   rmg::DBuf<double> tmp;          // composite temp
   rmg::DBuf<double> apbuf;        // Galerkin-product scratch (rows of [[A]][[P]]), all hierarchies
+  // device copies of a host composite CSR (rmg_operator_from_host_csr)
+  rmg::DBuf<int64_t> csr_rowptr, csr_col;
+  rmg::DBuf<double> csr_val;
 };

@@ -116,9 +116,24 @@ extern "C" rmg_status rmg_regional_apply_static(int dim, int nregions, const int
   }
   if (n_r >= (1LL << 31)) return static_fail(msg, msg_len, RMG_ERR_ARG, "too many regional nodes");
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+  // the work runs on the device of the caller's stream (the current device for the legacy
+  // default stream); that device is current for the rest of the call and the caller's device
+  // is restored on return
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess)
     return static_fail(msg, msg_len, RMG_ERR_CUDA, "cudaGetDevice failed");
+  int dev = prev;
+  if (st && cudaStreamGetDevice(st, &dev) != cudaSuccess)
+    return static_fail(msg, msg_len, RMG_ERR_CUDA, "cudaStreamGetDevice failed");
+  if (dev < 0 || dev >= kMaxDevices)
+    return static_fail(msg, msg_len, RMG_ERR_CUDA, "device index out of range");
+  if (dev != prev && cudaSetDevice(dev) != cudaSuccess)
+    return static_fail(msg, msg_len, RMG_ERR_CUDA, "cudaSetDevice failed");
+  struct RestoreDevice {
+    int prev, dev;
+    ~RestoreDevice() { if (dev != prev) cudaSetDevice(prev); }
+  } restore{prev, dev};
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -132,7 +147,6 @@ extern "C" rmg_status rmg_regional_apply_static(int dim, int nregions, const int
     }
     base = g_static_ptr[dev];
   }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   unsigned char* b = static_cast<unsigned char*>(base);
   RegionDev* tab = reinterpret_cast<RegionDev*>(b);
   int* dims_dev = reinterpret_cast<int*>(b + sizeof(RegionDev) * kStaticMaxRegions);

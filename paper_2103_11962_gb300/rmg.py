@@ -73,6 +73,7 @@ def lib():
         "rmg_operator_from_csr": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "rmg_operator_from_region_stencils": (ctypes.c_int, [P, ctypes.c_int, P]),
         "rmg_operator_from_block_csr": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P]),
+        "rmg_operator_from_host_csr": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P]),
         "rmg_hier_dofs_per_node": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_regional_apply": (ctypes.c_int, [P, P, P]),
         "rmg_comp_to_reg": (ctypes.c_int, [P, P, P]),
@@ -134,7 +135,8 @@ def exported_symbols():
             "rmg_hier_level_export", "rmg_hier_lambda", "rmg_hier_coarse_matrix",
             "rmg_hier_vcycle_launches", "rmg_launch_count", "rmg_hier_probe",
             "rmg_regional_apply_static", "rmg_hier_set_transfer_weights",
-            "rmg_operator_from_block_csr", "rmg_hier_dofs_per_node",
+            "rmg_operator_from_block_csr", "rmg_operator_from_host_csr",
+            "rmg_hier_dofs_per_node",
             "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor",
             "rmg_hier_tile_shape", "rmg_hier_coef_planes", "rmg_hier_galerkin",
             "rmg_mlp_num_params", "rmg_mlp_create",
@@ -167,6 +169,17 @@ def _ptr(t):
     if t is None:
         return None
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype):
+    """Address of a contiguous host array (CPU torch tensor or numpy array) of `dtype`."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"host array must be C-contiguous {np.dtype(dtype).name}")
+        return ctypes.c_void_p(a.ctypes.data)
+    if a.device.type != "cpu" or not a.is_contiguous() or a.element_size() != np.dtype(dtype).itemsize:
+        raise TypeError("host tensor must be a contiguous CPU tensor of the right type")
+    return ctypes.c_void_p(a.data_ptr())
 
 
 def default_options(**kw) -> Options:
@@ -240,6 +253,14 @@ class Layout:
     def operator_from_block_csr(self, stencil, dofs_per_node, rowptr, col, val):
         self.ctx.check(lib().rmg_operator_from_block_csr(self.h, stencil, dofs_per_node,
                                                          _ptr(rowptr), _ptr(col), _ptr(val)))
+
+    def operator_from_host_csr(self, stencil, dofs_per_node, rowptr, col, val):
+        """Split a composite CSR held in host memory (CPU torch tensors or numpy arrays of
+        int64 / int64 / float64; page-locked tensors give DMA copies)."""
+        self.ctx.check(lib().rmg_operator_from_host_csr(self.h, stencil, dofs_per_node,
+                                                        _host_ptr(rowptr, np.int64),
+                                                        _host_ptr(col, np.int64),
+                                                        _host_ptr(val, np.float64)))
 
     def operator_from_region_stencils(self, stencil, coeffs):
         self.ctx.check(lib().rmg_operator_from_region_stencils(self.h, stencil, _ptr(coeffs)))

@@ -132,6 +132,10 @@ def test_features_identical_on_copies(ctx):
 
 
 def test_mlp_forward_and_gradient_match_oracle(ctx):
+    """The forward outputs and every gradient entry against the oracle network with the same
+    BF16 roundings. The GPU accumulates in FP32 where the oracle uses FP64, so a hidden
+    activation can round to the neighbouring BF16 value (a relative step of 2^-8); such rare
+    flips bound the per-entry tolerances."""
     from oracle import learned as Lo
     from paper_2103_11962_gb300 import learned, rmg
     p = _hc()
@@ -148,14 +152,63 @@ def test_mlp_forward_and_gradient_match_oracle(ctx):
     net = rmg.MLP(ctx, params)
     out = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
     net.forward(X, out)
-    O_or, _ = Lo.forward(params.astype(np.float64), X.cpu().numpy().astype(np.float64))
-    assert np.abs(out.cpu().numpy() - O_or).max() <= 2e-3
+    Xh = X.cpu().numpy().astype(np.float64)
+    O_or, _ = Lo.forward(params.astype(np.float64), Xh)
+    d = np.abs(out.cpu().numpy() - O_or)
+    print(f"forward: max |O - O_or| = {d.max():.3e}, 99.9th pct {np.quantile(d, 0.999):.3e}")
+    assert d.max() <= 1e-3                         # every entry
+    assert np.quantile(d, 0.999) <= 1e-5           # all but BF16 rounding flips
     loss, g = net.gradient(X, Y, M)
-    L_or, g_or = Lo.loss_and_grad(params.astype(np.float64), X.cpu().numpy().astype(np.float64),
+    L_or, g_or = Lo.loss_and_grad(params.astype(np.float64), Xh,
                                   Y.cpu().numpy().astype(np.float64),
                                   M.cpu().numpy().astype(np.float64))
-    assert loss == pytest.approx(L_or, rel=1e-3)
-    assert np.linalg.norm(g - g_or) <= 1e-3 * np.linalg.norm(g_or)
+    assert loss == pytest.approx(L_or, rel=1e-4)
+    err = np.abs(g - g_or)
+    scale = np.abs(g_or).max()
+    print(f"gradient: max |g - g_or| / max |g_or| = {err.max() / scale:.3e}")
+    # every entry: 1e-3 of itself plus 1e-4 of the largest entry
+    assert np.all(err <= 1e-3 * np.abs(g_or) + 1e-4 * scale)
+
+
+def test_features_match_oracle(ctx):
+    """Network inputs of every regional node against the oracle's features of its composite
+    node (FP64 ratios, FP32 logarithms on the GPU)."""
+    from oracle import learned as Lo
+    for p in (_hc(), W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=5)):
+        dp, lay, h = _setup(ctx, p)
+        n_r = lay.sizes()["n_regional"]
+        feats = torch.empty((n_r, 32), dtype=torch.float32, device="cuda")
+        h.mlp_features(0, feats)
+        expect = Lo.features(p.A, p.global_dims)[p.region_gids]
+        got = feats.cpu().numpy().astype(np.float64)
+        assert np.abs(got - expect).max() <= 4e-6
+
+
+def test_predicted_weights_match_oracle(ctx):
+    """rmg_hier_mlp_weights against the oracle pipeline from the same parameters: oracle
+    features of the composite operator, the oracle network with the GPU's BF16 roundings,
+    zero weights along inactive axes. The features enter the network rounded to BF16, so a
+    feature that differs in its last FP32 bits can round the other way; the tolerance covers
+    such rare flips, and nearly every weight must agree to FP32-accumulation level."""
+    from oracle import learned as Lo
+    from paper_2103_11962_gb300 import learned, rmg
+    p = _hc()
+    dp, lay, h = _setup(ctx, p)
+    n_r = lay.sizes()["n_regional"]
+    params = learned.init_params(9)
+    net = rmg.MLP(ctx, params)
+    wr = torch.empty(3 * n_r, dtype=torch.float32, device="cuda")
+    h.mlp_weights(0, net, wr)
+    Fo = Lo.features(p.A, p.global_dims)
+    Oo, _ = Lo.forward(params.astype(np.float64), Fo)
+    expect = Lo.weights_from_outputs(Fo, Oo)[:, p.region_gids]
+    got = wr.view(3, n_r).cpu().numpy().astype(np.float64)
+    d = np.abs(got - expect)
+    print(f"weights: max diff {d.max():.3e}, 99.9th pct {np.quantile(d, 0.999):.3e}")
+    assert np.all((got == 0) == (expect == 0))
+    assert d.max() <= 2e-3
+    assert np.quantile(d, 0.999) <= 1e-5
+    net.close()
 
 
 def test_trained_network_against_plain_method(ctx):

@@ -76,3 +76,41 @@ def test_mixed_hierarchy_galerkin_products_in_fp32(ctx, name, precision):
         M = stencils_to_matrix(lev.layout.region_dims, coef.cpu().numpy(), kind)
         err = matrix_rel_diff(M, lev.Ar)
         assert err <= (1e-12 if l == 0 else 1e-5), (l, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_pcg_does_not_depend_on_rhs_scale(ctx, precision):
+    """Every CG inner product is FP64 and the FP32 cycle sees the residual scaled by a power of
+    two near 1/||b||: b times 2^-83 (about 1e-25) or 2^83 (about 1e25) gives the same
+    iterations and the solution times the same power of two, bit for bit; b times 1e-25 or
+    1e25 gives the same iterations and the same solution up to rounding."""
+    p, dp, lay, h = _gpu(ctx, "diff3d_small", "chebyshev", precision=precision)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    ref = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+    assert ref["converged"]
+    x_ref = x.clone()
+    for e in (-83, 83):
+        f = 2.0 ** e
+        x.zero_()
+        res = h.pcg(dp.b * f, x, rtol=1e-10, maxit=300)
+        assert res["converged"] and res["iterations"] == ref["iterations"], (e, res)
+        assert torch.equal(x, x_ref * f), e
+    for f in (1e-25, 1e25):
+        x.zero_()
+        res = h.pcg(dp.b * f, x, rtol=1e-10, maxit=300)
+        assert res["converged"] and res["iterations"] == ref["iterations"], (f, res)
+        assert res["true_relres"] <= 1e-10
+        assert torch.linalg.norm(x / f - x_ref) <= 1e-9 * torch.linalg.norm(x_ref)
+
+
+def test_converged_means_true_residual_passes(ctx):
+    """A reported convergence always holds for the true FP64 residual b - A x of the returned
+    iterate, in every precision."""
+    for precision in (0, 1, 2):
+        for name in ("c1_poisson2d", "diff3d_small", "highcontrast_small"):
+            p, dp, lay, h = _gpu(ctx, name, "chebyshev", precision=precision)
+            x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+            res = h.pcg(dp.b, x, rtol=1e-10, maxit=300)
+            assert res["converged"] and res["true_relres"] <= 1e-10, (precision, name, res)
+            r = p.b - p.A @ x.cpu().numpy()
+            assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(p.b) * (1 + 1e-6)

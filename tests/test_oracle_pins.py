@@ -787,3 +787,171 @@ def test_flexible_pcg_equals_pcg_for_a_symmetric_preconditioner():
     x2, it2, h2 = krylov.pcg(p.A, p.b, pre, rtol=1e-10, flexible=True)
     assert it1 == it2
     assert np.allclose(h1, h2, rtol=1e-6, atol=0)
+
+
+# ---------------------------------------------------------------------------- MLP forward pins
+# A hand-set network whose value is traced by hand. Layer-1 unit h reads feature (h + 1) mod 32
+# (units 32..63 have zero weights and bias -1, so ReLU keeps them at 0), layer-2 unit m reads
+# layer-1 unit (m + 7) mod 64, output j reads layer-2 unit 5 j + 2. So output j depends on the
+# single feature k(j) through units m = 5 j + 2, h = m + 7: j = 0 -> m 2, h 9, k 10;
+# j = 1 -> m 7, h 14, k 15; j = 2 -> m 12, h 19, k 20. All parameters and inputs are exact in
+# BF16 and every intermediate below stays exact in BF16, so the rounded and the exact network
+# give the same value.
+_HS_A = {9: 2.0, 14: 0.5, 19: -1.0}           # layer-1 weights of the used units
+_HS_B1 = {9: -0.25, 14: 0.75, 19: 0.5}
+_HS_C = {2: 1.5, 7: -2.0, 12: 0.25}           # layer-2 weights of the used units
+_HS_B2 = {2: 0.125, 7: 1.0, 12: -0.5}
+_HS_E = [-0.75, 3.0, 0.5]                     # output weights
+_HS_B3 = [0.5, -1.0, 0.25]
+
+
+def _handset_params():
+    from oracle import learned as Lm
+    W1 = np.zeros((64, 32)); b1 = np.full(64, -1.0)
+    for h in range(32):
+        W1[h, (h + 1) % 32] = _HS_A.get(h, 1.0)
+        b1[h] = _HS_B1.get(h, 0.0)
+    W2 = np.zeros((64, 64)); b2 = np.zeros(64)
+    for m in range(64):
+        W2[m, (m + 7) % 64] = _HS_C.get(m, 1.0)
+        b2[m] = _HS_B2.get(m, 0.0)
+    W3 = np.zeros((3, 64))
+    for j in range(3):
+        W3[j, 5 * j + 2] = _HS_E[j]
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), np.asarray(_HS_B3)])
+    assert p.size == Lm.NPARAMS
+    return p
+
+
+# Inputs: sample 0 keeps every used unit active; sample 1 drives layer-1 unit 9 negative (ReLU
+# zero); sample 2 drives layer-2 unit 7 negative.
+_HS_X = np.zeros((3, 32))
+_HS_X[0, [10, 15, 20]] = [0.375, 2.0, -1.5]
+_HS_X[1, [10, 15, 20]] = [-1.0, 0.5, 0.25]
+_HS_X[2, [10, 15, 20]] = [1.0, 6.0, 0.0]
+# Traced by hand, z3 of every (sample, output):
+#  s0 j0: h1 = relu(2*0.375 - 0.25) = 0.5,  h2 = relu(1.5*0.5 + 0.125) = 0.875, z3 = -0.75*0.875 + 0.5
+#  s0 j1: h1 = relu(0.5*2 + 0.75) = 1.75,   h2 = relu(-2*1.75 + 1) = 0,         z3 = -1
+#  s0 j2: h1 = relu(-1*-1.5 + 0.5) = 2,     h2 = relu(0.25*2 - 0.5) = 0,        z3 = 0.25
+#  s1 j0: h1 = relu(-2 - 0.25) = 0,         h2 = relu(0.125) = 0.125,           z3 = -0.75*0.125 + 0.5
+#  s1 j1: h1 = relu(0.25 + 0.75) = 1,       h2 = relu(-2 + 1) = 0,              z3 = -1
+#  s1 j2: h1 = relu(-0.25 + 0.5) = 0.25,    h2 = relu(0.0625 - 0.5) = 0,        z3 = 0.25
+#  s2 j0: h1 = relu(2 - 0.25) = 1.75,       h2 = relu(2.625 + 0.125) = 2.75,    z3 = -0.75*2.75 + 0.5
+#  s2 j1: h1 = relu(3 + 0.75) = 3.75,       h2 = relu(-7.5 + 1) = 0,            z3 = -1
+#  s2 j2: h1 = relu(0 + 0.5) = 0.5,         h2 = relu(0.125 - 0.5) = 0,         z3 = 0.25
+_HS_Z3 = np.array([[-0.15625, -1.0, 0.25],
+                   [0.40625, -1.0, 0.25],
+                   [-1.5625, -1.0, 0.25]])
+
+
+def _check_handset(forward):
+    p = _handset_params()
+    expect = 1.0 / (1.0 + np.exp(-_HS_Z3))
+    for rounding in (False, True):
+        O, _ = forward(p, _HS_X, rounding=rounding)
+        assert O.shape == (3, 3)
+        assert np.abs(O - expect).max() <= 1e-15, rounding
+
+
+def test_mlp_forward_handset_network():
+    from oracle import learned as Lm
+    _check_handset(Lm.forward)
+
+
+def _loop_forward(params, x):
+    """One sample through the network by explicit sums over the flat parameter layout of the
+    C header: W1[64][32] at 0, b1[64] at 2048, W2[64][64] at 2112, b2[64] at 6208, W3[3][64]
+    at 6272, b3[3] at 6464 (row = output unit, column = input unit)."""
+    import math
+    h1 = []
+    for h in range(64):
+        z = params[2048 + h]
+        for k in range(32):
+            z += params[h * 32 + k] * x[k]
+        h1.append(z if z > 0 else 0.0)
+    h2 = []
+    for m in range(64):
+        z = params[6208 + m]
+        for h in range(64):
+            z += params[2112 + m * 64 + h] * h1[h]
+        h2.append(z if z > 0 else 0.0)
+    out = []
+    for j in range(3):
+        z = params[6464 + j]
+        for m in range(64):
+            z += params[6272 + j * 64 + m] * h2[m]
+        out.append(1.0 / (1.0 + math.exp(-z)))
+    return out
+
+
+def test_mlp_forward_matches_per_sample_loop():
+    from oracle import learned as Lm
+    rng = np.random.default_rng(3)
+    params = rng.standard_normal(Lm.NPARAMS) * 0.4
+    X = rng.standard_normal((6, 32))
+    O, _ = Lm.forward(params, X, rounding=False)
+    for s in range(6):
+        assert np.abs(O[s] - np.asarray(_loop_forward(params, X[s]))).max() <= 1e-13
+
+
+@pytest.mark.parametrize("plant", ["transpose_w2", "swap_biases", "flip_w3", "transpose_w1"])
+def test_mlp_pins_catch_planted_mistakes(plant, monkeypatch):
+    """Each plausible slip in the oracle network makes the hand-set pin fail."""
+    from oracle import learned as Lm
+    real = Lm.unpack
+
+    def planted(params):
+        W1, b1, W2, b2, W3, b3 = real(params)
+        if plant == "transpose_w2":
+            W2 = W2.T
+        elif plant == "swap_biases":
+            b1, b2 = b2, b1
+        elif plant == "flip_w3":
+            W3 = -W3
+        else:
+            W1 = W1.T
+        return W1, b1, W2, b2, W3, b3
+
+    monkeypatch.setattr(Lm, "unpack", planted)
+    with pytest.raises((AssertionError, ValueError)):
+        _check_handset(Lm.forward)
+    with pytest.raises((AssertionError, ValueError)):
+        rng = np.random.default_rng(3)
+        params = rng.standard_normal(Lm.NPARAMS) * 0.4
+        x = rng.standard_normal((1, 32))
+        O, _ = Lm.forward(params, x, rounding=False)
+        assert np.abs(O[0] - np.asarray(_loop_forward(params, x[0]))).max() <= 1e-13
+
+
+def test_mlp_features_constant_laplacian_closed_form():
+    """Features of the constant-coefficient 7-point operator (couplings -h, diagonal 6h; masked
+    rows identity): a line of unmasked nodes gives log10(h / 6h) for every conductance and 0 for
+    every diagonal ratio; a line starting at the masked face x = 0 gives -12 for its first
+    conductance (a masked row has no coupling) and log10(1 / 6h) for its first diagonal."""
+    from oracle.learned import features
+    p = W.diffusion3d_7pt(region_grid=(2, 2, 1), choices=(10,), seed=0, sigma=0.0, rhs=False)
+    Nx, Ny, Nz = p.global_dims
+    h = 1.0 / (Nx - 1)
+    F = features(p.A, p.global_dims)
+    assert np.allclose(features(3.5 * p.A, p.global_dims), F, atol=1e-14)    # scale free
+    g = lambda x, y, z: x + Nx * (y + Ny * z)
+    inner = [np.log10(1 / 6)] * 3 + [0.0] * 4
+    # (4, 5, 4): x rem 1, y rem 2, z rem 1, every line inside the unmasked nodes
+    f = F[g(4, 5, 4)]
+    assert np.allclose(f[0:9], inner + [1 / 3, 1.0], atol=1e-14)
+    assert np.allclose(f[9:18], inner + [2 / 3, 1.0], atol=1e-14)
+    assert np.allclose(f[18:27], inner + [1 / 3, 1.0], atol=1e-14)
+    assert np.all(f[27:] == 0.0)
+    # (4, 5, 7): the z line ends at the masked face z = Nz - 1 = 9: its last conductance is
+    # -12 and its last diagonal ratio log10(1 / 6h)
+    f = F[g(4, 5, 7)]
+    expect_z = [np.log10(1 / 6), np.log10(1 / 6), -12.0, 0.0, 0.0, 0.0,
+                np.log10(1.0 / (6 * h)), 1 / 3, 1.0]
+    assert np.allclose(f[18:27], expect_z, atol=1e-13)
+    # (2, 6, 4): x line from the masked node x = 0; y on a coarse index (rem 0)
+    f = F[g(2, 6, 4)]
+    expect_x = [-12.0, np.log10(1 / 6), np.log10(1 / 6),
+                np.log10(1.0 / (6 * h)), 0.0, 0.0, 0.0, 2 / 3, 1.0]
+    assert np.allclose(f[0:9], expect_x, atol=1e-13)
+    assert np.all(f[9:18] == 0.0)
+    assert np.allclose(f[18:27], inner + [1 / 3, 1.0], atol=1e-14)

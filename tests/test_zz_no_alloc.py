@@ -25,7 +25,9 @@ def _rel(a, b):
 @pytest.mark.parametrize("factory", [
     lambda: W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=5),
     lambda: W.poisson2d_5pt(region_grid=(3, 2), n=28, seed=11),
-])
+    lambda: W.q1_laplace2d(region_grid=(2, 3), n=19, seed=12),
+    lambda: W.q1_laplace3d(region_grid=(2, 2, 2), n=10, seed=6),
+], ids=["7pt_3d", "5pt_2d", "9pt_2d", "27pt_3d"])
 def test_static_apply_matches_regular_apply(factory):
     from paper_2103_11962_gb300 import rmg, upload
     p = factory()
