@@ -38,3 +38,17 @@ def test_elasticity3d_on_device_equals_numpy():
     p = W.elasticity3d(region_grid=(2, 2, 2), choices=(10, 19), seed=4)
     d = D.elasticity3d(region_grid=(2, 2, 2), choices=(10, 19), seed=4, device="cpu")
     _same(p, d)
+
+
+def test_diffusion3d_7pt_on_device_equals_numpy():
+    from workloads import device as D
+    p = W.diffusion3d_7pt(region_grid=(2, 3, 2), choices=(10, 19), seed=1)
+    d = D.diffusion3d_7pt(region_grid=(2, 3, 2), choices=(10, 19), seed=1, device="cpu")
+    _same(p, d)
+
+
+def test_highcontrast3d_7pt_on_device_equals_numpy():
+    from workloads import device as D
+    p = W.highcontrast3d_7pt(region_grid=(3, 2, 2), choices=(10, 19), seed=3)
+    d = D.highcontrast3d_7pt(region_grid=(3, 2, 2), choices=(10, 19), seed=3, device="cpu")
+    _same(p, d)

@@ -230,3 +230,115 @@ def elasticity3d(region_grid=(8, 8, 8), choices=(28, 55), seed=95, sigma=0.5, nu
                           val, torch.from_numpy(b).to(device), 27,
                           dict(seed=seed, region_grid=tuple(region_grid), choices=tuple(choices),
                                sigma=sigma, nu=nu))
+
+
+def _edge_kappa_3d(kappa):
+    """Torch form of workloads._edge_kappa_3d: per axis, the mean coefficient of the (up to 4)
+    elements around each edge, added in the numpy order (slice 0, 1, 2, 3) and divided by the
+    count of elements present."""
+    import torch
+    Ez, Ey, Ex = kappa.shape
+    Nz, Ny, Nx = Ez + 1, Ey + 1, Ex + 1
+    dev = kappa.device
+    pad = torch.full((Ez + 2, Ey + 2, Ex + 2), float("nan"), dtype=torch.float64, device=dev)
+    pad[1:-1, 1:-1, 1:-1] = kappa
+
+    def nanmean(slices):
+        tot = torch.zeros_like(slices[0])
+        cnt = torch.zeros_like(slices[0])
+        for v in slices:
+            ok = ~torch.isnan(v)
+            tot = tot + torch.where(ok, v, torch.zeros((), dtype=v.dtype, device=dev))
+            cnt = cnt + ok.to(v.dtype)
+        return tot / cnt
+
+    ex = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device=dev)
+    ex[:, :, :Ex] = nanmean([pad[z0:z0 + Nz, y0:y0 + Ny, 1:Ex + 1]
+                             for z0 in (0, 1) for y0 in (0, 1)])
+    ey = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device=dev)
+    ey[:, :Ey, :] = nanmean([pad[z0:z0 + Nz, 1:Ey + 1, x0:x0 + Nx]
+                             for z0 in (0, 1) for x0 in (0, 1)])
+    ez = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device=dev)
+    ez[:Ez, :, :] = nanmean([pad[1:Ez + 1, y0:y0 + Ny, x0:x0 + Nx]
+                             for y0 in (0, 1) for x0 in (0, 1)])
+    return ex, ey, ez
+
+
+def _diffusion_csr(gdims, kappa, mask, device):
+    """Vertex-centred 7-point coefficients of workloads.diffusion3d_7pt_from_kappa, assembled
+    into CSR on the device."""
+    import torch
+    from . import OFFS7
+    Nx, Ny, Nz = gdims
+    h = 1.0 / (Nx - 1)
+    ekx, eky, ekz = _edge_kappa_3d(kappa)
+    vals = torch.zeros((7, Nz, Ny, Nx), dtype=torch.float64, device=device)
+    cx, cy, cz = -h * ekx, -h * eky, -h * ekz
+    del ekx, eky, ekz
+    vals[6] = cz
+    vals[5] = cy
+    vals[4] = cx
+    vals[2][:, :, 1:] = cx[:, :, :-1]
+    vals[1][:, 1:, :] = cy[:, :-1, :]
+    vals[0][1:, :, :] = cz[:-1, :, :]
+    del cx, cy, cz
+    vals[3] = -(vals[0] + vals[1] + vals[2] + vals[4] + vals[5] + vals[6])
+    maskt = torch.from_numpy(mask.astype(bool)).to(device)
+    return _csr_scalar(gdims, OFFS7, vals, maskt, device)
+
+
+def _rhs_device(rng, n, mask, device):
+    import torch
+    b = rng.uniform(-1.0, 1.0, size=n)
+    b[mask.astype(bool)] = 0.0
+    return torch.from_numpy(b).to(device)
+
+
+def diffusion3d_7pt(region_grid=(8, 8, 4), choices=(28, 55, 82), seed=1, sigma=1.0,
+                    device="cuda:0"):
+    """The 3D variable-coefficient diffusion of workloads.diffusion3d_7pt, assembled on the
+    device (slab sizes, kappa and b drawn on the host from the same Generator, in the same
+    order)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    slabs = tuple(tuple(int(v) for v in rng.choice(np.asarray(choices), size=k))
+                  for k in region_grid)
+    gdims, rdims, gids = region_map(slabs)
+    Nx, Ny, Nz = gdims
+    kappa = torch.from_numpy(np.exp(sigma * rng.standard_normal(size=(Nz - 1, Ny - 1, Nx - 1)))
+                             ).to(device)
+    mask = boundary_mask(gdims)
+    rowptr, col, val = _diffusion_csr(gdims, kappa, mask, device)
+    del kappa
+    b = _rhs_device(rng, Nx * Ny * Nz, mask, device)
+    return DeviceWorkload("diffusion3d_7pt", 3, 1, gdims, slabs, rdims, gids, mask, rowptr,
+                          col, val, b, 7, dict(seed=seed, region_grid=tuple(region_grid),
+                                               choices=tuple(choices), sigma=sigma))
+
+
+def highcontrast3d_7pt(region_grid=(7, 7, 7), choices=(28, 55, 82), seed=3,
+                       log10_range=(-3.0, 3.0), device="cuda:0"):
+    """The high-contrast diffusion of workloads.highcontrast3d_7pt (kappa constant per region,
+    log-uniform), assembled on the device."""
+    import torch
+    from . import slab_origins
+    rng = np.random.default_rng(seed)
+    slabs = tuple(tuple(int(v) for v in rng.choice(np.asarray(choices), size=k))
+                  for k in region_grid)
+    gdims, rdims, gids = region_map(slabs)
+    Nx, Ny, Nz = gdims
+    kreg = 10.0 ** rng.uniform(log10_range[0], log10_range[1], size=tuple(region_grid)[::-1])
+    kappa = torch.empty((Nz - 1, Ny - 1, Nx - 1), dtype=torch.float64, device=device)
+    ox, oy, oz = (slab_origins(s) for s in slabs)
+    for c, nz in enumerate(slabs[2]):
+        for bb, ny in enumerate(slabs[1]):
+            for a, nx in enumerate(slabs[0]):
+                kappa[oz[c]:oz[c] + nz - 1, oy[bb]:oy[bb] + ny - 1, ox[a]:ox[a] + nx - 1] = \
+                    float(kreg[c, bb, a])
+    mask = boundary_mask(gdims)
+    rowptr, col, val = _diffusion_csr(gdims, kappa, mask, device)
+    del kappa
+    b = _rhs_device(rng, Nx * Ny * Nz, mask, device)
+    return DeviceWorkload("highcontrast3d_7pt", 3, 1, gdims, slabs, rdims, gids, mask, rowptr,
+                          col, val, b, 7, dict(seed=seed, region_grid=tuple(region_grid),
+                                               choices=tuple(choices), kappa_region=kreg))
