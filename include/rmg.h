@@ -95,10 +95,14 @@ typedef struct {
  * launch covers all regions of a level with blocks of 256 threads, each block one tile of one
  * region. Shape 0: runs of 256 consecutive regional nodes. Shapes 1..8: boxes tx x ty x tz of
  * (32,8,1), (64,4,1), (128,2,1), (16,16,1), (32,4,2), (16,8,2), (16,4,4), (8,8,4); in 2D only
- * the tz = 1 boxes apply. With -1 the first numeric setup times every applicable shape on
- * every smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps
- * the fastest; the choice does not change any result (each node computes the same row). */
-#define RMG_NUM_TILE_SHAPES 9
+ * the tz = 1 boxes apply. Shape 9: z-marching warp columns (a warp takes 32 consecutive nodes
+ * of one row of a region and steps through all its z-planes, keeping three planes of u in
+ * registers and taking x-neighbours by warp shuffles); it applies to the half-plane sweeps of
+ * the FP32 cycle's level 0 for 3D 7- and 27-point stencils (rmg_hier_tile_shape reports it as
+ * 32 x 1 x nz, nz = 0). With -1 the first numeric setup times every applicable shape on every
+ * smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps the
+ * fastest; the choice does not change any result (each node computes the same row). */
+#define RMG_NUM_TILE_SHAPES 10
 
 typedef struct {
   int iterations;        /* products with A (0 when the initial residual already passes)  */

@@ -82,26 +82,51 @@ __global__ void k_dense_scaled32(int nd, const double* __restrict__ A,
     M[(size_t)i * nd + j] = (float)(si * A[(size_t)i * nd + j] * s[j]);
 }
 
-// w = FP32(s .* r)
-__global__ void k_scale_vec32(int nd, const double* __restrict__ s, const double* __restrict__ r,
-                              float* __restrict__ w) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x)
-    w[i] = (float)(s[i] * r[i]);
+// w = FP32(s .* r * 2^-e) with 2^e near max |s_i r_i|, and back = 2^e: the FP32 solve then
+// sees values of order one whatever the scale of r (no FP32 underflow or overflow), and the
+// scaling is exact. One block of 1024 threads (the coarse dimension is at most 16384).
+__global__ void __launch_bounds__(1024)
+k_scale_vec32(int nd, const double* __restrict__ s, const double* __restrict__ r,
+              float* __restrict__ w, double* __restrict__ back) {
+  __shared__ double red[32];
+  __shared__ double pw;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) m = fmax(m, fabs(s[i] * r[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = red[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      const int e = (m > 0.0 && m <= 1.7e308) ? ilogb(m) : 0;
+      pw = ldexp(1.0, -e);
+      *back = ldexp(1.0, e);
+    }
+  }
+  __syncthreads();
+  const double p = pw;
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) w[i] = (float)(s[i] * r[i] * p);
 }
 
-// x = s .* (M w) (accumulate = 0) or x += s .* (M w): one warp per row, FP32 products and sums.
+// x = s .* (M w) * back (accumulate = 0) or x += s .* (M w) * back: one warp per row, FP32
+// products and sums; back undoes the power-of-two scaling of w.
 __global__ void k_gemv32(int nd, const float* __restrict__ M, const float* __restrict__ w,
-                         const double* __restrict__ s, double* __restrict__ x, int accumulate) {
+                         const double* __restrict__ s, const double* __restrict__ back,
+                         double* __restrict__ x, int accumulate) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const double bk = *back;
   for (int i = warp; i < nd; i += nwarps) {
     float acc = 0.f;
     const float* row = M + (size_t)i * nd;
     for (int j = lane; j < nd; j += 32) acc = fmaf(row[j], w[j], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[i] = (accumulate ? x[i] : 0.0) + s[i] * (double)acc;
+    if (lane == 0) x[i] = (accumulate ? x[i] : 0.0) + s[i] * ((double)acc * bk);
   }
 }
 
@@ -709,7 +734,7 @@ void hier_build(Hier& h) {
   h.Dblk.alloc(nblk * kNB * kNB);
   h.M32.alloc(nd * nd); h.Ainv32.alloc(nd * nd); h.Linv32.alloc(nd * nd); h.Tinv32.alloc(nd * nd);
   h.Dblk32.alloc(nblk * kNB * kNB);
-  h.cscale.alloc(nd); h.cres.alloc(nd); h.cw32.alloc(nd); h.cnorm.alloc(4); h.cerr.alloc(1);
+  h.cscale.alloc(nd); h.cres.alloc(nd); h.cw32.alloc(nd); h.cnorm.alloc(5); h.cerr.alloc(1);
   h.xc.alloc(nd); h.rc.alloc(nd);
   RMG_CUDA(cudaMemsetAsync(h.xc.get(), 0, h.xc.bytes(), c.stream));
   RMG_CUDA(cudaStreamSynchronize(c.stream));
@@ -1038,12 +1063,13 @@ static void coarse_factor_fp64(Hier& h, int nc) {
 // before every refinement step.
 static int mixed_coarse_solve(Hier& h, cudaStream_t st, int nd, int steps, double* nrm) {
   Ctx& c = *h.c;
-  const int eg = std::max(1, std::min(c.nsm * 4, (nd + 255) / 256));
   const int wg = std::max(1, std::min(c.nsm * 4, (nd * 32 + 255) / 256));
   int launches = 0;
-  k_scale_vec32<<<eg, 256, 0, st>>>(nd, h.cscale.get(), h.rc.get(), h.cw32.get());
+  double* back = h.cnorm.get() + 4;
+  k_scale_vec32<<<1, 1024, 0, st>>>(nd, h.cscale.get(), h.rc.get(), h.cw32.get(), back);
   RMG_LAUNCHED();
-  k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), h.xc.get(), 0);
+  k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), back,
+                               h.xc.get(), 0);
   RMG_LAUNCHED();
   launches += 2;
   for (int k = 0; k < steps; ++k) {
@@ -1053,10 +1079,10 @@ static int mixed_coarse_solve(Hier& h, cudaStream_t st, int nd, int steps, doubl
       k_norm2_dense<<<1, 256, 0, st>>>(nd, h.cres.get(), nrm + k);
       RMG_LAUNCHED();
     }
-    k_scale_vec32<<<eg, 256, 0, st>>>(nd, h.cscale.get(), h.cres.get(), h.cw32.get());
+    k_scale_vec32<<<1, 1024, 0, st>>>(nd, h.cscale.get(), h.cres.get(), h.cw32.get(), back);
     RMG_LAUNCHED();
-    k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), h.xc.get(),
-                                 1);
+    k_gemv32<<<wg, 256, 0, st>>>(nd, h.Ainv32.get(), h.cw32.get(), h.cscale.get(), back,
+                                 h.xc.get(), 1);
     RMG_LAUNCHED();
     launches += 3;
   }
@@ -1153,13 +1179,23 @@ static void make_low_precision(Hier& h) {
 
 // ---------------------------------------------------------------------- tile-shape autotuner
 // Candidate tile shapes of the stencil sweeps: index 0 = runs of kTile consecutive nodes,
-// 1.. = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty). Boxes hand every
-// thread its (i, j, l) without a decode and keep stencil neighbours inside the block, at the
-// price of idle threads where a box overhangs the region; which wins depends on the region
+// 1..8 = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty), 9 = z-marching
+// warp columns (k_stencil_zm). Boxes hand every thread its (i, j, l) without a decode and keep
+// stencil neighbours inside the block, at the price of idle threads where a box overhangs the
+// region; z-marching keeps u of three planes in registers; which wins depends on the region
 // sizes, the stencil and the precision, so each hierarchy times them.
 
-static bool shape_fits(const Level& L, int k) {
+static bool shape_fits(const Hier& h, int l, int k) {
+  const Level& L = *h.lv[l];
   const TileShape t = kTileShapes[k];
+  if (k == kZMarchShape) {      // FP32 half-plane sweeps of 3D 7/27-point stencils only
+    if (!(h.half(l) != nullptr && L.B == 1 && L.dim == 3 && (L.kind == 7 || L.kind == 27) &&
+          h.o.smoother != RMG_SMOOTHER_GS))
+      return false;
+    for (int d : L.hdims)
+      if (d >= 32768) return false;                       // segment and row are 16-bit
+    return true;
+  }
   if (t.lx < 0) return true;
   if (L.dim == 2 && t.lx + t.ly != 8) return false;      // 2D levels need tz = 1
   for (int d : L.hdims)
@@ -1171,13 +1207,22 @@ static void set_shape(Hier& h, int l, int k) {
   Level& L = *h.lv[l];
   h.shape[l] = k;
   const TileShape t = kTileShapes[k];
-  if (t.lx < 0) {
+  if (t.lx == -1) {
     h.sgrid[l] = L.grid();
     return;
   }
-  const int tx = 1 << t.lx, ty = 1 << t.ly, tz = kTile >> (t.lx + t.ly);
   std::vector<Tile> tl;
-  for (int r = 0; r < L.nreg; ++r) {
+  if (t.lx == -2) {
+    // z-marching warp columns: one task per (region, 32-node segment of a row, row)
+    for (int r = 0; r < L.nreg; ++r) {
+      const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1];
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; x += 32) tl.push_back(Tile{r, 0, (short)x, (short)y, 0, 0});
+    }
+  }
+  const int tx = t.lx < 0 ? 1 : 1 << t.lx, ty = t.lx < 0 ? 1 : 1 << t.ly;
+  const int tz = t.lx < 0 ? 1 : kTile >> (t.lx + t.ly);
+  for (int r = 0; r < L.nreg && t.lx >= 0; ++r) {
     const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1], nz = L.hdims[3 * r + 2];
     for (int z = 0; z < nz; z += tz)
       for (int y = 0; y < ny; y += ty)
@@ -1213,13 +1258,13 @@ static void autotune_t(Hier& h) {
     RMG_CUDA(cudaMemsetAsync(V.u.get(), 0, nv * sizeof(VT), st));
     RMG_CUDA(cudaMemsetAsync(V.b.get(), 0, nv * sizeof(VT), st));
     if (h.o.tile_shape >= 0) {
-      set_shape(h, l, shape_fits(L, h.o.tile_shape) ? h.o.tile_shape : 0);
+      set_shape(h, l, shape_fits(h, l, h.o.tile_shape) ? h.o.tile_shape : 0);
       continue;
     }
     int best = 0;
     float best_ms = 0.f;
     for (int k = 0; k < kNumTileShapes; ++k) {
-      if (!shape_fits(L, k)) continue;
+      if (!shape_fits(h, l, k)) continue;
       set_shape(h, l, k);
       auto run = [&]() {
         launch_stencil(c, L, ex.coef(l), (const VT*)V.u.get(), V.y.get(),
@@ -1251,6 +1296,10 @@ static void autotune(Hier& h) {
 }
 
 void tile_shape(const Hier& h, int l, int* tx, int* ty, int* tz) {
+  if (h.shape[l] == kZMarchShape) {
+    *tx = 32; *ty = 1; *tz = 0;
+    return;
+  }
   const TileShape t = kTileShapes[h.shape[l]];
   *tx = t.lx < 0 ? 0 : 1 << t.lx;
   *ty = t.lx < 0 ? 0 : 1 << t.ly;

@@ -109,3 +109,26 @@ def test_fp32_cycle_at_bench_region_sizes(ctx, name):
     assert res["converged"] and res["true_relres"] <= 1e-10
     assert res["iterations"] <= it_or + 3
     assert np.linalg.norm(x.cpu().numpy() - x_or) <= 1e-6 * np.linalg.norm(x_or)
+
+
+@pytest.mark.parametrize("name", list(SAMPLES))
+def test_fp32_tile_shapes_identical_at_bench_region_sizes(ctx, name):
+    """Runs, a box shape and the z-marching warp columns (several warps per row of 55- and
+    82-node regions, so the warp-edge fix-ups are exercised) give the same FP32 cycle bit for
+    bit, with the half planes in use."""
+    p, levels, mg = _sample(name)
+    ref = None
+    for shape in (0, 8, 9):
+        dp, lay, h = _gpu(ctx, p, 1, shape)
+        assert h.coef_planes(0) == (p.stencil + 1) // 2
+        if shape == 9:
+            assert h.tile_shape(0) == (32, 1, 0)
+        z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+        h.vcycle(dp.b, z)
+        zc = z.cpu().numpy()
+        if ref is None:
+            ref = zc
+        else:
+            assert np.array_equal(zc, ref), shape
+        h.close()
+        lay.close()
