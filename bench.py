@@ -95,6 +95,11 @@ WORKLOADS = {
                             "(profiling size)"),
     "c2_quarter": dict(CHEB, l2="inputs larger than L2",
                        desc="C2-shaped 3D 7-point diffusion on 4x4x2 regions (profiling size)"),
+    "offset_heldout": dict(CHEB, l2="inputs larger than L2",
+                           desc="3D 7-point diffusion, 4x4x4 regions with per-axis node counts "
+                                "from {28,55} (seed 77), kappa log-uniform in [1e-3, 1e3] on "
+                                "8x8x8 boxes whose faces lie off the coarse-grid planes (held "
+                                "out from the learned prolongator's training family)"),
     "c5_elasticity": dict(CHEB, power_iters=30, l2="inputs larger than L2",
                           desc="3D linear elasticity, Q1 hexahedra, 3 dofs per node, 3x3x3 "
                                "regions of 28^3 nodes (the paper's 82^3 elasticity mesh), E "
@@ -129,14 +134,21 @@ def make_problem(name, dev):
         return WD.elasticity3d(region_grid=(8, 8, 8), choices=(28, 55), seed=95, device=dev)
     if name == "c5_elasticity":
         return W.elasticity3d(region_grid=(3, 3, 3), choices=(28,), seed=4)
+    if name == "offset_heldout":
+        return W.highcontrast3d_offset(region_grid=(4, 4, 4), choices=(28, 55), seed=77, blocks=8)
     return W.config(name)
 
 
-def training_family(workload):
-    """Seeded small operators the learned prolongator is trained on (same PDE family)."""
+def training_family(family):
+    """Seeded small operators the learned prolongator is trained on: 2x2x2 regions of 10^3
+    nodes of the workload's PDE family (seeds 1000 + s for the high-contrast family, as the
+    C4 configuration prescribes)."""
     import workloads as W
-    if workload.startswith("c4"):
+    if family == "c4":
         return lambda s: W.highcontrast3d_7pt(region_grid=(2, 2, 2), choices=(10,), seed=1000 + s)
+    if family == "offset":
+        return lambda s: W.highcontrast3d_offset(region_grid=(2, 2, 2), choices=(10,),
+                                                 seed=5000 + s)
     return lambda s: W.diffusion3d_7pt(region_grid=(2, 2, 2), choices=(10, 19, 28), seed=2000 + s)
 
 
@@ -688,6 +700,86 @@ def e2e_leg(B, wl, prec, K, W_):
                                           "rmg_pcg_solve, host buffers page-locked"}
 
 
+def learned_leg(B, wl, family, n_train, K, W_, prec="fp32"):
+    """The learned prolongator on a workload: train on n_train seeded operators of `family`
+    (labelled by the plain method's two-grid error reduction, outside the timed region), then
+    time steps with three level-0 transfers: plain (linear interpolation), learned everywhere
+    (the network's weights at every node), and per-region acceptance (learned weights kept
+    where a region's energy reduction is no worse than linear, linear elsewhere; the plain
+    prolongator if the blend is globally worse). Inside a timed learned step the network
+    predicts the weights from the freshly split operator before the numeric setup."""
+    import numpy as np
+    from paper_2103_11962_gb300 import learned
+    torch = B.torch
+    t0 = time.perf_counter()
+    F, Y, M, factors = learned.training_set(B.ctx, range(n_train), training_family(family),
+                                            device=B.dev, batch=50)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net, hist = learned.train(B.ctx, F, Y, M, steps=2000, batch=16384, lr=2e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"family": family, "train_operators": n_train, "samples": int(F.shape[0]),
+           "teacher_better_fraction": float(np.mean(factors[:, 1] < factors[:, 0])),
+           "label_s": t1 - t0, "train_s": t2 - t1, "loss_first": float(hist[0]),
+           "loss_last": float(hist[-1])}
+    del F, Y, M
+    p = wl.p
+    n_r = p.n_regional_nodes
+    h = wl.hierarchy(prec)
+    wr = torch.empty(3 * n_r, dtype=torch.float32, device=B.dev)
+    mixed = torch.empty_like(wr)
+
+    def run(kind, accept=None):
+        def step():
+            wl.set_operator()
+            if kind == "plain":
+                h.set_transfer_weights(0, None)
+            elif kind == "teacher":
+                h.opdep_weights(0, wr)
+                h.set_transfer_weights(0, wr)
+            else:
+                h.mlp_weights(0, net, wr)
+                if kind == "per_region":
+                    h.blend_weights(0, accept, wr, mixed)
+                    h.set_transfer_weights(0, mixed)
+                else:
+                    h.set_transfer_weights(0, wr)
+            h.setup_numeric()
+            wl.x.zero_()
+            return h.pcg(wl.dp.b, wl.x, rtol=RTOL, maxit=500, history=False)
+        ms, infos, _ = B.timed(step, K, W_, wl.flush)
+        i = infos[-1]
+        return {"ms_per_step": ms / K, "pcg_iterations": i["iterations"],
+                "true_relres": i["true_relres"], "converged": i["converged"],
+                "value": job_value(p.n_unknowns * i["vcycles"] * K, B.world, ms)}
+
+    out["plain"] = run("plain")
+    out["plain"]["factor"] = h.convergence_factor(6, 7)
+    out["teacher"] = run("teacher")
+    out["teacher"]["factor"] = h.convergence_factor(6, 7)
+    out["learned_all"] = run("learned_all")
+    out["learned_all"]["factor"] = h.convergence_factor(6, 7)
+    h.mlp_weights(0, net, wr)
+    acc = learned.accept_per_region(h, wr, n_r, device=B.dev)
+    if acc["accepted"]:
+        # the region decisions of the acceptance run, reapplied in every timed step
+        out["per_region"] = run("per_region", acc["accept"])
+    else:
+        out["per_region"] = dict(out["plain"], note="no region kept the learned weights, or the "
+                                                    "blend was globally worse: plain prolongator")
+    out["per_region"].update(regions=acc["regions"], regions_accepted=acc["regions_accepted"],
+                             colour_classes=acc["colours"],
+                             factor=acc["factor"], factor_candidate=acc["factor_candidate"],
+                             factor_blended=acc["factor_blended"])
+    fp = out["plain"]["ms_per_step"]
+    for k in ("teacher", "learned_all", "per_region"):
+        out[k]["speedup_vs_plain"] = fp / out[k]["ms_per_step"]
+    h.close()
+    net.close()
+    return out
+
+
 def variant_errors_vs_oracle(B, x_oracle_path, sample_key):
     """||x - x_oracle|| / ||x_oracle|| of every precision on the oracle's sample (the sample the
     CPU baseline solved), and on the 4x4x4-region C3 slice against the stored oracle solution
@@ -788,7 +880,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-oracle-errors", action="store_true")
-    ap.add_argument("--train-operators", type=int, default=40)
+    ap.add_argument("--train-operators", type=int, default=2000)
     ap.add_argument("--json-out", default=None, help="also write the JSON line to this file")
     ap.add_argument("--rap-table", action="store_true",
                     help="time the Galerkin triple product alone on the single-region 2D "
@@ -875,7 +967,28 @@ def main():
                                          "problem": swl.problem_info(),
                                          "steps": args.sub_steps, "warmup": max(3, args.warmup),
                                          "precisions": srecs}
+                if sname.startswith("c4") and not args.no_learned:
+                    try:
+                        out["configs"][sname]["learned"] = learned_leg(
+                            B, swl, "c4", args.train_operators, args.sub_steps,
+                            max(3, args.warmup))
+                    except Exception as ex:
+                        out["configs"][sname]["learned"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
                 swl.close()
+                if sname.startswith("c4") and not args.no_learned:
+                    # held out: jumps off the coarse planes, where the teacher beats linear
+                    # interpolation (on C4 the jumps sit on coarse planes and it cannot)
+                    try:
+                        hwl = Workload(B, "offset_heldout")
+                        out["configs"][sname]["learned_held_out"] = dict(
+                            learned_leg(B, hwl, "offset", args.train_operators // 4,
+                                        args.sub_steps, max(3, args.warmup)),
+                            config=workload_config("offset_heldout"),
+                            problem=hwl.problem_info())
+                        hwl.close()
+                    except Exception as ex:
+                        out["configs"][sname]["learned_held_out"] = {
+                            "error": f"{type(ex).__name__}: {ex}"[:300]}
             except Exception as ex:
                 out["configs"][sname] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
 

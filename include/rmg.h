@@ -95,14 +95,10 @@ typedef struct {
  * launch covers all regions of a level with blocks of 256 threads, each block one tile of one
  * region. Shape 0: runs of 256 consecutive regional nodes. Shapes 1..8: boxes tx x ty x tz of
  * (32,8,1), (64,4,1), (128,2,1), (16,16,1), (32,4,2), (16,8,2), (16,4,4), (8,8,4); in 2D only
- * the tz = 1 boxes apply. Shape 9: z-marching warp columns (a warp takes 32 consecutive nodes
- * of one row of a region and steps through all its z-planes, keeping three planes of u in
- * registers and taking x-neighbours by warp shuffles); it applies to the half-plane sweeps of
- * the FP32 cycle's level 0 for 3D 7- and 27-point stencils (rmg_hier_tile_shape reports it as
- * 32 x 1 x nz, nz = 0). With -1 the first numeric setup times every applicable shape on every
- * smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps the
- * fastest; the choice does not change any result (each node computes the same row). */
-#define RMG_NUM_TILE_SHAPES 10
+ * the tz = 1 boxes apply. With -1 the first numeric setup times every applicable shape on
+ * every smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps
+ * the fastest; the choice does not change any result (each node computes the same row). */
+#define RMG_NUM_TILE_SHAPES 9
 
 typedef struct {
   int iterations;        /* products with A (0 when the initial residual already passes)  */
@@ -294,6 +290,33 @@ rmg_status rmg_hier_mlp_weights(rmg_hier* hier, int level, rmg_mlp* mlp, float* 
  * vectors of the hierarchy. */
 rmg_status rmg_hier_convergence_factor(rmg_hier* hier, int iters, unsigned long long seed,
                                        double* factor);
+
+/* Per-region error energies of the V-cycle as a stationary solver, for accepting learned
+ * interpolation region by region (no counterpart in the paper). From a SplitMix64 random error
+ * e (stream `seed`, zero at masked nodes) the cycle runs `iters` times, e <- e - M^-1 A e. For
+ * every region k, e0[k] and eK[k] (host double[nregions]) receive E_k(e) = e_k^T A^(k) e_k
+ * before and after: the region matrix of the split (Sec. 4) applied to the region's copy of e,
+ * without the interface sum. By Lemma 1 the E_k add up to e^T A e, and for M-matrix operators
+ * (non-positive couplings, row sums zero or positive) every A^(k) is positive semi-definite,
+ * so (eK[k] / e0[k])^(1 / (2 iters)) is the region's share of the A-norm reduction. Scalar
+ * operators only. Uses the PCG work vectors; synchronises. */
+rmg_status rmg_hier_region_energies(rmg_hier* hier, int iters, unsigned long long seed,
+                                    double* e0, double* eK);
+/* Stored transfer weights (device float[3 * n_r(level)], the layout of
+ * rmg_hier_set_transfer_weights) that take `learned` (same layout) at every node all of whose
+ * regions accept (accept: host uint8[nregions(level)], nonzero = accept) and linear
+ * interpolation (rem / 3, rounded to FP32) elsewhere, zero along axes where the node sits on a
+ * coarse index. The copies of an interface node lie in the same regions, so they receive
+ * identical weights, as Lemma 2 requires. Synchronises. */
+rmg_status rmg_hier_blend_weights(rmg_hier* hier, int level, const uint8_t* accept,
+                                  const float* learned, float* out);
+
+/* A colouring of the regions (host int colours[nregions], *ncolours = number of colours) in
+ * which regions that share a composite node get different colours (greedy, region order). A
+ * transfer changed only in the regions of one colour, blended with rmg_hier_blend_weights,
+ * leaves every interface node and every other region's rows unchanged, so its effect can be
+ * measured region by region without neighbours interfering. Synchronises. */
+rmg_status rmg_hier_region_colours(rmg_hier* hier, int* colours, int* ncolours);
 
 /* One regional V-cycle with zero initial guess, z = M^-1 r: the regional mgCycle of the
  * figure in Sec. 3.6 with the operations of Sec. 3.3 (smoothing with the regional residual,

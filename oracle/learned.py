@@ -177,3 +177,25 @@ def weights_from_outputs(feats, out) -> np.ndarray:
     F = np.asarray(feats)
     O = np.asarray(out)
     return np.stack([np.where(F[:, 9 * a + 8] > 0.5, O[:, a], 0.0) for a in range(3)])
+
+
+def blend_weights(region_dims, region_gids, accept, learned, dim) -> np.ndarray:
+    """(3, n_r) regional weights: `learned` (3, n_r) at regional nodes whose composite node lies
+    only in accepting regions, linear interpolation rem/3 (as FP32) elsewhere, 0 along axes
+    where the node sits on a coarse index (local coordinate divisible by 3)."""
+    dims = np.asarray(region_dims).reshape(-1, 3)
+    sizes = dims.prod(axis=1)
+    reg = np.repeat(np.arange(dims.shape[0]), sizes)
+    gids = np.asarray(region_gids)
+    ok_comp = np.ones(int(gids.max()) + 1, dtype=bool)
+    np.logical_and.at(ok_comp, gids, np.asarray(accept, dtype=bool)[reg])
+    ok = ok_comp[gids]
+    local = np.concatenate([np.arange(s) for s in sizes])
+    nx, ny = dims[reg, 0], dims[reg, 1]
+    coord = [local % nx, (local // nx) % ny, local // (nx * ny)]
+    out = np.zeros((3, gids.size))
+    for a in range(3):
+        rem = coord[a] % 3 if a < dim else np.zeros_like(local)
+        lin = np.where(rem == 1, np.float32(1.0 / 3.0), np.float32(2.0 / 3.0)).astype(np.float64)
+        out[a] = np.where(rem == 0, 0.0, np.where(ok, np.asarray(learned)[a], lin))
+    return out

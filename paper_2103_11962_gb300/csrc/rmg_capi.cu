@@ -325,6 +325,32 @@ rmg_status rmg_hier_convergence_factor(rmg_hier* hh, int iters, unsigned long lo
   });
 }
 
+rmg_status rmg_hier_region_energies(rmg_hier* hh, int iters, unsigned long long seed,
+                                    double* e0, double* eK) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(iters > 0 && e0 && eK, RMG_ERR_ARG, "bad arguments");
+    region_energies(hh->h, iters, seed, e0, eK);
+  });
+}
+
+rmg_status rmg_hier_blend_weights(rmg_hier* hh, int level, const uint8_t* accept,
+                                  const float* learned, float* out) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(accept && learned && out, RMG_ERR_ARG, "bad arguments");
+    blend_weights(hh->h, level, accept, learned, out);
+  });
+}
+
+rmg_status rmg_hier_region_colours(rmg_hier* hh, int* colours, int* ncolours) {
+  if (!hh) return RMG_ERR_ARG;
+  return guarded(hh->h.layout->ctx, [&] {
+    RMG_REQUIRE(colours && ncolours, RMG_ERR_ARG, "bad arguments");
+    *ncolours = region_colours(hh->h, colours);
+  });
+}
+
 rmg_status rmg_hier_galerkin(rmg_hier* hh, int level) {
   if (!hh) return RMG_ERR_ARG;
   return guarded(hh->h.layout->ctx, [&] { galerkin_level(hh->h, level); });

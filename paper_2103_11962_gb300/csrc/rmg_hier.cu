@@ -776,7 +776,7 @@ static void galerkin_t(Hier& h, int l, const Level& F, Level& C, const T* fcoef,
   T* cco = ccoef + (size_t)blk * C.kind * C.n_r;
   const double mdiag = (blk / F.B == blk % F.B) ? 1.0 : 0.0;
 #define RMG_RAP(FK, CK, D)                                                                    \
-  if (sizeof(T) == 4 && (FK == 5 || FK == 7)) {                                               \
+  if (sizeof(T) == 4) {                                                                       \
     k_ap_axis32<FK, D><<<gf, kTile, 0, c.stream>>>(Gf, C.regions.get(), (const float*)fco,     \
                                                    F.mask.get(), C.mask.get(), (float*)ap);   \
   } else {                                                                                    \
@@ -1179,23 +1179,14 @@ static void make_low_precision(Hier& h) {
 
 // ---------------------------------------------------------------------- tile-shape autotuner
 // Candidate tile shapes of the stencil sweeps: index 0 = runs of kTile consecutive nodes,
-// 1..8 = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty), 9 = z-marching
-// warp columns (k_stencil_zm). Boxes hand every thread its (i, j, l) without a decode and keep
-// stencil neighbours inside the block, at the price of idle threads where a box overhangs the
-// region; z-marching keeps u of three planes in registers; which wins depends on the region
+// 1.. = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty). Boxes hand every
+// thread its (i, j, l) without a decode and keep stencil neighbours inside the block, at the
+// price of idle threads where a box overhangs the region; which wins depends on the region
 // sizes, the stencil and the precision, so each hierarchy times them.
 
 static bool shape_fits(const Hier& h, int l, int k) {
   const Level& L = *h.lv[l];
   const TileShape t = kTileShapes[k];
-  if (k == kZMarchShape) {      // FP32 half-plane sweeps of 3D 7/27-point stencils only
-    if (!(h.half(l) != nullptr && L.B == 1 && L.dim == 3 && (L.kind == 7 || L.kind == 27) &&
-          h.o.smoother != RMG_SMOOTHER_GS))
-      return false;
-    for (int d : L.hdims)
-      if (d >= 32768) return false;                       // segment and row are 16-bit
-    return true;
-  }
   if (t.lx < 0) return true;
   if (L.dim == 2 && t.lx + t.ly != 8) return false;      // 2D levels need tz = 1
   for (int d : L.hdims)
@@ -1207,22 +1198,13 @@ static void set_shape(Hier& h, int l, int k) {
   Level& L = *h.lv[l];
   h.shape[l] = k;
   const TileShape t = kTileShapes[k];
-  if (t.lx == -1) {
+  if (t.lx < 0) {
     h.sgrid[l] = L.grid();
     return;
   }
+  const int tx = 1 << t.lx, ty = 1 << t.ly, tz = kTile >> (t.lx + t.ly);
   std::vector<Tile> tl;
-  if (t.lx == -2) {
-    // z-marching warp columns: one task per (region, 32-node segment of a row, row)
-    for (int r = 0; r < L.nreg; ++r) {
-      const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1];
-      for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; x += 32) tl.push_back(Tile{r, 0, (short)x, (short)y, 0, 0});
-    }
-  }
-  const int tx = t.lx < 0 ? 1 : 1 << t.lx, ty = t.lx < 0 ? 1 : 1 << t.ly;
-  const int tz = t.lx < 0 ? 1 : kTile >> (t.lx + t.ly);
-  for (int r = 0; r < L.nreg && t.lx >= 0; ++r) {
+  for (int r = 0; r < L.nreg; ++r) {
     const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1], nz = L.hdims[3 * r + 2];
     for (int z = 0; z < nz; z += tz)
       for (int y = 0; y < ny; y += ty)
@@ -1296,10 +1278,6 @@ static void autotune(Hier& h) {
 }
 
 void tile_shape(const Hier& h, int l, int* tx, int* ty, int* tz) {
-  if (h.shape[l] == kZMarchShape) {
-    *tx = 32; *ty = 1; *tz = 0;
-    return;
-  }
   const TileShape t = kTileShapes[h.shape[l]];
   *tx = t.lx < 0 ? 0 : 1 << t.lx;
   *ty = t.lx < 0 ? 0 : 1 << t.ly;
@@ -1455,6 +1433,188 @@ double convergence_factor(Hier& h, int iters, unsigned long long seed) {
   }
   if (!(e0 > 0.0) || iters <= 0) return 0.0;
   return std::pow(std::max(ek, 0.0) / e0, 0.5 / iters);
+}
+
+// ---------------------------------------------------------------------- per-region energies
+// E_k(e) = e_k^T A^(k) e_k for every region k: the region's own (split) matrix applied to the
+// region's copy of e, without the interface sum. By Lemma 1 the E_k add up to e^T A e; for the
+// M-matrix operators here every A^(k) is positive semi-definite (row sums zero or positive,
+// non-positive couplings), so E_k is a local energy of the error. One partial sum per run tile,
+// then the tiles of each region (contiguous in the tile list) in order.
+template <int KIND>
+__global__ void __launch_bounds__(kTile)
+k_region_energy(Grid G, const double* __restrict__ coef, const double* __restrict__ e,
+                double* __restrict__ part) {
+  for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) {
+    const Tile tile = G.tiles[t];
+    const RegionDev R = G.regions[tile.region];
+    const int li = tile.start + (int)threadIdx.x;
+    double v = 0.0;
+    if (li < R.nx * R.ny * R.nz) {
+      int i, j, l;
+      decode(li, R, i, j, l);
+      const int n = R.off + li;
+      v = e[n] * stencil_row<KIND, double, double, double>(coef, e, n, G.n_r, i, j, l, R);
+    }
+    v = block_sum<kTile>(v);
+    if (threadIdx.x == 0) part[t] = v;
+  }
+}
+
+__global__ void k_region_sum(int nreg, const int* __restrict__ tstart,
+                             const double* __restrict__ part, double* __restrict__ out) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int t = tstart[r]; t < tstart[r + 1]; ++t) s += part[t];
+    out[r] = s;
+  }
+}
+
+static void region_energy(Hier& h, const double* e, double* host_out) {
+  Ctx& c = *h.c;
+  const Level& L = *h.lv[0];
+  const Grid G = L.grid();
+  if (h.energy_tiles.n != (size_t)L.nreg + 1) {
+    std::vector<int> ts(L.nreg + 1, 0);
+    for (size_t t = 0; t < L.htiles.size(); ++t) ts[L.htiles[t].region + 1] = (int)t + 1;
+    for (int r = 0; r < L.nreg; ++r) ts[r + 1] = std::max(ts[r + 1], ts[r]);
+    h.energy_tiles.alloc(L.nreg + 1);
+    RMG_CUDA(cudaMemcpy(h.energy_tiles.get(), ts.data(), ts.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+    h.energy_part.alloc(std::max<size_t>(1, L.htiles.size()));
+    h.energy_out.alloc(L.nreg);
+  }
+  const int gb = persistent_grid(c, G.ntiles);
+  switch (L.kind) {
+    case 5: k_region_energy<5><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), e, h.energy_part.get()); break;
+    case 7: k_region_energy<7><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), e, h.energy_part.get()); break;
+    case 9: k_region_energy<9><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), e, h.energy_part.get()); break;
+    default: k_region_energy<27><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), e, h.energy_part.get()); break;
+  }
+  RMG_LAUNCHED();
+  k_region_sum<<<persistent_grid(c, (L.nreg + 255) / 256), 256, 0, c.stream>>>(
+      L.nreg, h.energy_tiles.get(), h.energy_part.get(), h.energy_out.get());
+  RMG_LAUNCHED();
+  RMG_CUDA(cudaMemcpyAsync(host_out, h.energy_out.get(), (size_t)L.nreg * sizeof(double),
+                           cudaMemcpyDeviceToHost, c.stream));
+  RMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// The V-cycle as a stationary solver (as convergence_factor) with the region energies of the
+// error before and after `iters` cycles.
+void region_energies(Hier& h, int iters, unsigned long long seed, double* e0, double* eK) {
+  require_dense(h);
+  Ctx& c = *h.c;
+  cudaStream_t st = c.stream;
+  const Level& L0 = *h.lv[0];
+  RMG_REQUIRE(L0.B == 1, RMG_ERR_ARG, "region energies are for scalar operators");
+  const int n = L0.n_r, eg = persistent_grid(c, (n + 255) / 256);
+  double* e = h.x.get();
+  double* Ae = h.v64[0].b.get();
+  double* z = h.v64[0].u.get();
+  k_power_init<<<eg, 256, 0, st>>>(L0.n_r, L0.B, L0.gid.get(), L0.mask.get(), seed, e);
+  RMG_LAUNCHED();
+  region_energy(h, e, e0);
+  for (int k = 0; k < iters; ++k) {
+    launch_stencil(c, L0, L0.coef.get(), e, h.v64[0].y.get(), EpiStore<double>{Ae}, st, nullptr);
+    if (h.mixed()) {
+      k_convert<double, float><<<eg, 256, 0, st>>>((size_t)n, Ae, h.v32[0].b.get());
+      RMG_LAUNCHED();
+      vcycle(h);
+      k_convert<float, double><<<eg, 256, 0, st>>>((size_t)n, h.v32[0].u.get(), z);
+      RMG_LAUNCHED();
+    } else {
+      vcycle(h);
+    }
+    k_axpy_neg<<<eg, 256, 0, st>>>(n, z, e);
+    RMG_LAUNCHED();
+  }
+  region_energy(h, e, eK);
+}
+
+// Transfer weights of a level from `learned` where every region containing the node accepts,
+// linear interpolation (rem / 3) elsewhere; zero along axes where the node sits on a coarse
+// index. Copies of an interface node see the same regions, so they get the same weights.
+__global__ void __launch_bounds__(kTile)
+k_blend_weights(Grid G, int dim, const uint8_t* __restrict__ accept,
+                const uint8_t* __restrict__ mult, const int* __restrict__ gid,
+                const int* __restrict__ cgrp, const int* __restrict__ gptr,
+                const int* __restrict__ gslot, const float* __restrict__ learned,
+                float* __restrict__ out) {
+  RMG_FOR_NODES(G)
+    int x[3];
+    decode(li, R, x[0], x[1], x[2]);
+    bool ok = accept[tile_.region] != 0;
+    if (ok && mult[n] > 1) {
+      const int grp = cgrp[gid[n]];
+      for (int q = gptr[grp]; q < gptr[grp + 1]; ++q)
+        ok = ok && accept[region_of(G.regions, G.nreg, gslot[q])] != 0;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int rem = a < dim ? x[a] % 3 : 0;
+      const size_t k = (size_t)a * G.n_r + n;
+      out[k] = rem == 0 ? 0.f : (ok ? learned[k] : (rem == 1 ? (float)(1.0 / 3.0)
+                                                             : (float)(2.0 / 3.0)));
+    }
+  RMG_END_FOR_NODES
+}
+
+void blend_weights(Hier& h, int level, const uint8_t* accept_host, const float* learned,
+                   float* out) {
+  RMG_REQUIRE(level >= 0 && level + 1 < h.levels(), RMG_ERR_ARG,
+              "transfer weights exist for levels 0 .. levels-2");
+  Level& L = *h.lv[level];
+  RMG_REQUIRE(L.B == 1, RMG_ERR_ARG, "stored transfer weights are for scalar operators");
+  Ctx& c = *h.c;
+  h.accept.ensure(L.nreg);
+  RMG_CUDA(cudaMemcpyAsync(h.accept.get(), accept_host, (size_t)L.nreg, cudaMemcpyHostToDevice,
+                           c.stream));
+  const Grid G = L.grid();
+  k_blend_weights<<<persistent_grid(c, G.ntiles), kTile, 0, c.stream>>>(
+      G, L.dim, h.accept.get(), L.mult.get(), L.gid.get(), L.cgrp.get(), L.gptr.get(),
+      L.gslot.get(), learned, out);
+  RMG_LAUNCHED();
+  RMG_CUDA(cudaStreamSynchronize(c.stream));      // the host accept array may be reused
+}
+
+// Greedy colouring of the region graph of level 0: two regions are adjacent when they share a
+// composite node (an interface group holds copies in both). Regions of one colour never touch,
+// so a transfer changed in the regions of one colour alone leaves every interface node with
+// linear weights (rmg_hier_blend_weights) and the other regions' own rows unchanged.
+int region_colours(Hier& h, int* colours) {
+  const Level& L = *h.lv[0];
+  std::vector<int> gptr(L.ngroups + 1), gslot(L.nslots);
+  if (L.ngroups) {
+    RMG_CUDA(cudaMemcpy(gptr.data(), L.gptr.get(), gptr.size() * sizeof(int),
+                        cudaMemcpyDeviceToHost));
+    RMG_CUDA(cudaMemcpy(gslot.data(), L.gslot.get(), gslot.size() * sizeof(int),
+                        cudaMemcpyDeviceToHost));
+  }
+  auto region = [&](int slot) {
+    return (int)(std::upper_bound(L.hoff.begin(), L.hoff.begin() + L.nreg, slot) -
+                 L.hoff.begin()) - 1;
+  };
+  std::vector<std::vector<int>> adj(L.nreg);
+  for (int g = 0; g < L.ngroups; ++g)
+    for (int a = gptr[g]; a < gptr[g + 1]; ++a)
+      for (int b = a + 1; b < gptr[g + 1]; ++b) {
+        const int ra = region(gslot[a]), rb = region(gslot[b]);
+        if (ra != rb) { adj[ra].push_back(rb); adj[rb].push_back(ra); }
+      }
+  int ncol = 0;
+  std::vector<int> col(L.nreg, -1);
+  for (int r = 0; r < L.nreg; ++r) {
+    std::vector<char> used(ncol + 1, 0);
+    for (int q : adj[r])
+      if (col[q] >= 0) used[col[q]] = 1;
+    int c = 0;
+    while (used[c]) ++c;
+    col[r] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  std::copy(col.begin(), col.end(), colours);
+  return ncol;
 }
 
 // ---------------------------------------------------------------------- PCG

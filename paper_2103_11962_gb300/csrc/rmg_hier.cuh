@@ -16,13 +16,11 @@ struct LevelVecs {
   }
 };
 
-// Stencil-sweep tile shapes (index 0: runs of kTile consecutive nodes; 1..8: boxes
-// 2^lx x 2^ly x kTile / 2^(lx + ly); 9: z-marching warp columns, lx = -2), in the order
-// rmg_options.tile_shape numbers them.
+// Stencil-sweep tile shapes (index 0: runs of kTile consecutive nodes; 1..: boxes
+// 2^lx x 2^ly x kTile / 2^(lx + ly)), in the order rmg_options.tile_shape numbers them.
 struct TileShape { int lx, ly; };
 constexpr TileShape kTileShapes[] = {{-1, 0}, {5, 3}, {6, 2}, {7, 1}, {4, 4},
-                                     {5, 2}, {4, 3}, {4, 2}, {3, 3}, {-2, 0}};
-constexpr int kZMarchShape = 9;
+                                     {5, 2}, {4, 3}, {4, 2}, {3, 3}};
 constexpr int kNumTileShapes = (int)(sizeof(kTileShapes) / sizeof(kTileShapes[0]));
 static_assert(kNumTileShapes == RMG_NUM_TILE_SHAPES, "tile shape table and header disagree");
 
@@ -76,6 +74,10 @@ struct Hier {
   long long probe_count = 0;
   // learned-prolongator inference scratch (features and network outputs)
   DBuf<float> mlp_feats, mlp_out;
+  // per-region energies (tile ranges, tile partials, region sums) and accepted regions
+  DBuf<int> energy_tiles;
+  DBuf<double> energy_part, energy_out;
+  DBuf<uint8_t> accept;
   // PCG work vectors (regional, FP64)
   DBuf<double> x, r, z, p, q, zold, tmp;
   DBuf<float> zold32;                        // previous FP32 cycle output (flexible CG)
@@ -110,6 +112,10 @@ void set_transfer_weights(Hier& h, int level, const float* wr);
 void opdep_weights(Hier& h, int level, float* wr);
 void constant_weights(Hier& h, int level, float* wr);
 double convergence_factor(Hier& h, int iters, unsigned long long seed);
+void region_energies(Hier& h, int iters, unsigned long long seed, double* e0, double* eK);
+void blend_weights(Hier& h, int level, const uint8_t* accept_host, const float* learned,
+                   float* out);
+int region_colours(Hier& h, int* colours);
 void pcg_solve(Hier& h, const double* b, double* x, double rtol, int maxit, double* history,
                rmg_solve_info* info);
 

@@ -146,8 +146,36 @@ __device__ __forceinline__ float stencil_row_half(const float* __restrict__ half
   using S = Sten<KIND>;
   static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
   constexpr int C = S::CENTER;
-  float au = 0.f;
   const int sy = R.nx, sz = R.nx * R.ny;
+#ifndef RMG_HALF_GATHER
+#define RMG_HALF_GATHER 1
+#endif
+  if constexpr (!(RMG_HALF_GATHER && S::S >= 9)) {
+    // 5/7-point rows: load and multiply slot by slot (the compiler keeps them at 32 registers)
+    float au = 0.f;
+#pragma unroll
+    for (int s = 0; s < S::S; ++s) {
+      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+      bool ok = true;
+      if (dx < 0) ok &= (i > 0);
+      if (dx > 0) ok &= (i < R.nx - 1);
+      if (dy < 0) ok &= (j > 0);
+      if (dy > 0) ok &= (j < R.ny - 1);
+      if (dz < 0) ok &= (l > 0);
+      if (dz > 0) ok &= (l < R.nz - 1);
+      if (ok) {
+        const int nb = n + dx + dy * sy + dz * sz;
+        const float c = s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
+                              : half[(size_t)(s - C) * (size_t)n_r + n];
+        au = fmaf(c, u[nb], au);
+      }
+    }
+    return au;
+  } else {
+  // 9/27-point rows: all coefficient and neighbour loads of the row first (independent, so
+  // they are in flight together), then the products in slot order
+  float cv[S::S], uv[S::S];
+  bool okv[S::S];
 #pragma unroll
   for (int s = 0; s < S::S; ++s) {
     const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
@@ -158,14 +186,19 @@ __device__ __forceinline__ float stencil_row_half(const float* __restrict__ half
     if (dy > 0) ok &= (j < R.ny - 1);
     if (dz < 0) ok &= (l > 0);
     if (dz > 0) ok &= (l < R.nz - 1);
-    if (ok) {
-      const int nb = n + dx + dy * sy + dz * sz;
-      const float c = s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
-                            : half[(size_t)(s - C) * (size_t)n_r + n];
-      au = fmaf(c, u[nb], au);
-    }
+    okv[s] = ok;
+    const int nb = n + dx + dy * sy + dz * sz;
+    cv[s] = ok ? (s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
+                        : half[(size_t)(s - C) * (size_t)n_r + n])
+               : 0.f;
+    uv[s] = ok ? u[nb] : 0.f;
   }
+  float au = 0.f;
+#pragma unroll
+  for (int s = 0; s < S::S; ++s)
+    if (okv[s]) au = fmaf(cv[s], uv[s], au);
   return au;
+  }
 }
 
 // Half planes of a float stencil; *asym becomes 1 when a mirrored pair inside a region differs
@@ -219,229 +252,21 @@ __device__ __forceinline__ void stencil_pass(const Grid& G, const float* __restr
   RMG_END_FOR_NODES
 }
 
+// Resident blocks per SM the half-plane sweeps may be compiled for (unset: the compiler's
+// own register choice).
+#ifdef RMG_HALF_MIN_BLOCKS
+#define RMG_HALF_BOUNDS __launch_bounds__(kTile, RMG_HALF_MIN_BLOCKS)
+#else
+#define RMG_HALF_BOUNDS __launch_bounds__(kTile)
+#endif
+
 template <int KIND, class Epi>
-__global__ void __launch_bounds__(kTile)
+__global__ void RMG_HALF_BOUNDS
 k_stencil_half(Grid G, const float* __restrict__ coef, const float* __restrict__ half,
                const int* __restrict__ asym, const float* __restrict__ u,
                const uint8_t* __restrict__ mult, float* __restrict__ y, Epi epi) {
   if (*asym) stencil_pass<false, KIND>(G, coef, u, mult, y, epi);
   else stencil_pass<true, KIND>(G, half, u, mult, y, epi);
-}
-
-// ---- z-marching sweep of the FP32 half planes (3D, 7- and 27-point) -----------------------
-// The work unit is one warp: lanes hold 32 consecutive x-nodes i = x0 + lane of row j of one
-// region and march through all z-planes l of the region together. u of the planes l - 1, l and
-// l + 1 stays in registers, so each step loads only plane l + 1 (and, for the 7-point stencil,
-// the rows j -/+ 1 of plane l). A value at x +/- 1 is the neighbouring lane's own value
-// (warp shuffle); the two lanes at the warp edges fetch the one past the warp. Every global
-// load is therefore at the lane's own x (coalesced, aligned to the warp's first node) apart
-// from one two-lane fix-up per row. The mirrored coefficients of the half form (slot s < C of
-// node n is half plane S-1-s-C at n + off(s)) come the same way: the plane-(l - 1) ones of the
-// node's own column from the previous step's registers, those of x-neighbours by shuffle.
-// Each node forms the same products in the same order as stencil_row / stencil_row_half, so
-// the results are bit for bit those of the other tile shapes.
-constexpr unsigned kFullMask = 0xffffffffu;
-
-// Values at x - 1, x, x + 1 of row n (the lane's node in that row), taking the x - 1 value
-// from array aL, x from aC and x + 1 from aR: each lane loads aL, aC, aR at its own node
-// (when `row` holds and the lane is inside the region) and the x-neighbours arrive by shuffle.
-// fixL / fixR: lane 0 must fetch aL[n - 1] itself (i > 0), lane 31 aR[n + 1] (i + 1 < nx).
-__device__ __forceinline__ void zm_triple(const float* __restrict__ aL,
-                                          const float* __restrict__ aC,
-                                          const float* __restrict__ aR, int n, bool row, bool in,
-                                          bool fixL, bool fixR, int lane, float& vl, float& vc,
-                                          float& vr) {
-  const bool ld = row && in;
-  const float oL = ld ? aL[n] : 0.f;
-  vc = (aC == aL) ? oL : (ld ? aC[n] : 0.f);
-  const float oR = (aR == aL) ? oL : (ld ? aR[n] : 0.f);
-  vl = __shfl_up_sync(kFullMask, oL, 1);
-  vr = __shfl_down_sync(kFullMask, oR, 1);
-  if (row && ((lane == 0 && fixL) || (lane == 31 && fixR))) {
-    const float f = lane == 0 ? aL[n - 1] : aR[n + 1];
-    if (lane == 0) vl = f; else vr = f;
-  }
-}
-
-// One value per lane and its x-neighbours' values of the same quantity (already in registers),
-// with the warp-edge fix-ups read from a[n - 1] / a[n + 1].
-__device__ __forceinline__ void zm_neighbours(float own, const float* __restrict__ aL,
-                                              const float* __restrict__ aR, int n, bool row,
-                                              bool fixL, bool fixR, int lane, float ownL,
-                                              float ownR, float& vl, float& vr) {
-  vl = __shfl_up_sync(kFullMask, ownL, 1);
-  vr = __shfl_down_sync(kFullMask, ownR, 1);
-  (void)own;
-  if (row && ((lane == 0 && fixL) || (lane == 31 && fixR))) {
-    const float f = lane == 0 ? aL[n - 1] : aR[n + 1];
-    if (lane == 0) vl = f; else vr = f;
-  }
-}
-
-template <class Epi>
-__device__ __forceinline__ void zm_store(bool in, int n, float au,
-                                         const uint8_t* __restrict__ mult, float* __restrict__ y,
-                                         const Epi& epi) {
-  if (in) {
-    if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
-  }
-}
-
-// 27-point: half plane p holds slot 13 + p; slot s < 13 of node n is half plane 13 - s at
-// n + off(s).
-template <class Epi>
-__device__ __forceinline__ void zm_column27(const RegionDev& R, int i, int j, int lane,
-                                            const float* __restrict__ half,
-                                            const float* __restrict__ u,
-                                            const uint8_t* __restrict__ mult,
-                                            float* __restrict__ y, const Epi& epi, int n_r) {
-  const int sy = R.nx, sz = R.nx * R.ny;
-  const bool in = i < R.nx;
-  const bool xm = i > 0, xp = i < R.nx - 1, ym = j > 0, yp = j < R.ny - 1;
-  const bool fixL = i > 0, fixR = i + 1 < R.nx;
-  auto H = [&](int p) { return half + (size_t)p * (size_t)n_r; };
-  float U[3][3][3];                  // [dz + 1][dy + 1][dx + 1] around the current node
-  int n = R.off + i + sy * j;        // node of plane l (out of the region for idle lanes)
-  // planes l - 1 (none yet) and l = 0
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) U[0][b][a] = 0.f;
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    const bool row = dy < 0 ? ym : (dy > 0 ? yp : true);
-    zm_triple(u, u, u, n + dy * sy, row, in, fixL, fixR, lane, U[1][dy + 1][0], U[1][dy + 1][1],
-              U[1][dy + 1][2]);
-  }
-  float pv8 = 0.f, pv9 = 0.f, pv10 = 0.f;   // own half planes 8, 9, 10 at plane l - 1
-  for (int l = 0; l < R.nz; ++l, n += sz) {
-    const bool zm = l > 0, zp = l < R.nz - 1;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const bool row = zp && (dy < 0 ? ym : (dy > 0 ? yp : true));
-      zm_triple(u, u, u, n + sz + dy * sy, row, in, fixL, fixR, lane, U[2][dy + 1][0],
-                U[2][dy + 1][1], U[2][dy + 1][2]);
-    }
-    float c[27];
-#pragma unroll
-    for (int p = 0; p < 14; ++p) c[13 + p] = in ? H(p)[n] : 0.f;
-    // mirrored, plane l - 1: rows j - 1, j, j + 1
-    zm_triple(H(13), H(12), H(11), n - sz - sy, zm && ym, in, fixL, fixR, lane, c[0], c[1], c[2]);
-    zm_neighbours(pv9, H(10), H(8), n - sz, zm, fixL, fixR, lane, pv10, pv8, c[3], c[5]);
-    c[4] = pv9;
-    zm_triple(H(7), H(6), H(5), n - sz + sy, zm && yp, in, fixL, fixR, lane, c[6], c[7], c[8]);
-    // mirrored, plane l: row j - 1, and the x - 1 neighbour of row j
-    zm_triple(H(4), H(3), H(2), n - sy, ym, in, fixL, fixR, lane, c[9], c[10], c[11]);
-    float dummy;
-    zm_neighbours(c[14], H(1), H(1), n, true, fixL, false, lane, c[14], c[14], c[12], dummy);
-    float au = 0.f;
-#pragma unroll
-    for (int s = 0; s < 27; ++s) {
-      const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-      bool ok = true;
-      if (dx < 0) ok &= xm;
-      if (dx > 0) ok &= xp;
-      if (dy < 0) ok &= ym;
-      if (dy > 0) ok &= yp;
-      if (dz < 0) ok &= zm;
-      if (dz > 0) ok &= zp;
-      if (ok) au = fmaf(c[s], U[dz + 1][dy + 1][dx + 1], au);
-    }
-    zm_store(in, n, au, mult, y, epi);
-    pv8 = c[21];
-    pv9 = c[22];
-    pv10 = c[23];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        U[0][b][a] = U[1][b][a];
-        U[1][b][a] = U[2][b][a];
-      }
-  }
-}
-
-// 7-point, slots (-z, -y, -x, 0, +x, +y, +z): half plane p holds slot 3 + p (centre, +x, +y,
-// +z); the -z coefficient of node n is half plane 3 at n - sz (the previous step's own value),
-// -y is half plane 2 at n - sy, -x is half plane 1 at n - 1 (the left lane's own value).
-template <class Epi>
-__device__ __forceinline__ void zm_column7(const RegionDev& R, int i, int j, int lane,
-                                           const float* __restrict__ half,
-                                           const float* __restrict__ u,
-                                           const uint8_t* __restrict__ mult,
-                                           float* __restrict__ y, const Epi& epi, int n_r) {
-  const int sy = R.nx, sz = R.nx * R.ny;
-  const bool in = i < R.nx;
-  const bool xm = i > 0, xp = i < R.nx - 1, ym = j > 0, yp = j < R.ny - 1;
-  const bool fixL = i > 0, fixR = i + 1 < R.nx;
-  auto H = [&](int p) { return half + (size_t)p * (size_t)n_r; };
-  int n = R.off + i + sy * j;
-  float um = 0.f;                        // u at plane l - 1
-  float uc = in ? u[n] : 0.f;            // u at plane l
-  float pv3 = 0.f;                       // own half plane 3 at plane l - 1
-  for (int l = 0; l < R.nz; ++l, n += sz) {
-    const bool zm = l > 0, zp = l < R.nz - 1;
-    const float up = (zp && in) ? u[n + sz] : 0.f;
-    const float uym = (ym && in) ? u[n - sy] : 0.f;
-    const float uyp = (yp && in) ? u[n + sy] : 0.f;
-    float uxm, uxp;
-    zm_neighbours(uc, u, u, n, true, fixL, fixR, lane, uc, uc, uxm, uxp);
-    float c[7];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) c[3 + p] = in ? H(p)[n] : 0.f;
-    c[0] = pv3;
-    c[1] = (ym && in) ? H(2)[n - sy] : 0.f;
-    float dummy;
-    zm_neighbours(c[4], H(1), H(1), n, true, fixL, false, lane, c[4], c[4], c[2], dummy);
-    const float v[7] = {um, uym, uxm, uc, uxp, uyp, up};
-    const bool ok[7] = {zm, ym, xm, true, xp, yp, zp};
-    float au = 0.f;
-#pragma unroll
-    for (int s = 0; s < 7; ++s)
-      if (ok[s]) au = fmaf(c[s], v[s], au);
-    zm_store(in, n, au, mult, y, epi);
-    pv3 = c[6];
-    um = uc;
-    uc = up;
-  }
-}
-
-// Phase A over z-marching warp units (Grid::lx == -2; tiles[t] = {region, -, x0, row j}). When
-// the pack found the operator asymmetric (*asym != 0) every lane computes its column on the full
-// planes instead.
-// Resident blocks per SM the z-marching kernels are compiled for (the 27-point one needs about
-// 90 registers a thread at 2 blocks; 3 blocks cap it at 80 with a few spilled values).
-#ifndef RMG_ZM_MIN_BLOCKS
-#define RMG_ZM_MIN_BLOCKS 2
-#endif
-
-template <int KIND, class Epi>
-__global__ void __launch_bounds__(kTile, RMG_ZM_MIN_BLOCKS)
-k_stencil_zm(Grid G, const float* __restrict__ coef, const float* __restrict__ half,
-             const int* __restrict__ asym, const float* __restrict__ u,
-             const uint8_t* __restrict__ mult, float* __restrict__ y, Epi epi) {
-  static_assert(KIND == 7 || KIND == 27, "z-marching sweeps are 3D 7- and 27-point");
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const bool full = *asym != 0;
-  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < G.ntiles; t += gridDim.x * wpb) {
-    const Tile tile = G.tiles[t];
-    const RegionDev R = G.regions[tile.region];
-    const int i = tile.x0 + lane, j = tile.y0;
-    if (full) {
-      if (i >= R.nx) continue;
-      for (int l = 0; l < R.nz; ++l) {
-        const int n = R.off + i + R.nx * (j + R.ny * l);
-        const float au = stencil_row<KIND, float, float, float>(coef, u, n, G.n_r, i, j, l, R);
-        if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
-      }
-      continue;
-    }
-    if (KIND == 27)
-      zm_column27(R, i, j, lane, half, u, mult, y, epi, G.n_r);
-    else
-      zm_column7(R, i, j, lane, half, u, mult, y, epi, G.n_r);
-  }
 }
 
 // Phase B: interface groups. y holds the partial row results of every copy. One thread per

@@ -64,17 +64,7 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
   bool done = false;
   if constexpr (std::is_same<CT, float>::value && std::is_same<VT, float>::value &&
                 std::is_same<AT, float>::value) {
-    if (half && L.B == 1 && G.lx == -2) {
-      RMG_REQUIRE(asym != nullptr && (L.kind == 7 || L.kind == 27), RMG_ERR_STATE,
-                  "z-marching sweeps need half planes of a 7- or 27-point stencil");
-      const int nt = (G.ntiles + kTile / 32 - 1) / (kTile / 32);
-      const uint8_t* mu = L.mult.get();
-      if (L.kind == 7)
-        launch_resident(c, k_stencil_zm<7, Epi>, nt, st, G, coef, half, asym, u, mu, y, epi);
-      else
-        launch_resident(c, k_stencil_zm<27, Epi>, nt, st, G, coef, half, asym, u, mu, y, epi);
-      done = true;
-    } else if (half && L.B == 1) {
+    if (half && L.B == 1) {
       RMG_REQUIRE(asym != nullptr, RMG_ERR_STATE, "half planes without their flag");
       const int nt = G.ntiles;
       const uint8_t* mu = L.mult.get();
@@ -87,7 +77,6 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
       done = true;
     }
   }
-  RMG_REQUIRE(done || G.lx != -2, RMG_ERR_STATE, "z-marching tiles outside a half-plane sweep");
   if (done) {
   } else if (L.B == 1) {
     switch (L.kind) {

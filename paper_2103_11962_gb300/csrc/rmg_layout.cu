@@ -349,8 +349,19 @@ __device__ __forceinline__ void box_offset(int d, int sy, int sz, int& dx, int& 
 // interior rows the stores of one entry index are contiguous). A slot that receives no entry
 // is zeroed at the end; the diagonal slot takes the nullspace rule; a repeated column (not
 // produced by a well-formed CSR) is accumulated.
+// Resident blocks per SM the split may be compiled for (unset: the compiler's own register
+// choice), and the entries whose loads it batches.
+#ifdef RMG_SPLIT_MIN_BLOCKS
+#define RMG_SPLIT_BOUNDS __launch_bounds__(kTile, RMG_SPLIT_MIN_BLOCKS)
+#else
+#define RMG_SPLIT_BOUNDS __launch_bounds__(kTile)
+#endif
+#ifndef RMG_SPLIT_BATCH
+#define RMG_SPLIT_BATCH 4
+#endif
+
 template <int KIND, int B>
-__global__ void __launch_bounds__(kTile)
+__global__ void RMG_SPLIT_BOUNDS
 k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
             const int* __restrict__ c2r, const int* __restrict__ cgrp,
             const int* __restrict__ gptr, const int* __restrict__ gslot,
@@ -376,7 +387,7 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
     const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
     // entries in batches of four: the column, value and group loads of a batch are issued
     // together (they do not depend on each other), then the entries are applied in order
-    constexpr int U = 4;
+    constexpr int U = RMG_SPLIT_BATCH;
     for (int64_t eb = e0; eb < e1; eb += U) {
       int64_t cc[U];
       double vv[U];

@@ -127,12 +127,13 @@ k_ap(Grid Gf, const RegionDev* __restrict__ cregs, const T* __restrict__ fcoef,
   RMG_END_FOR_NODES
 }
 
-// A P for a 5/7-point fine stencil in FP32, for the mixed hierarchies: every output o of the
+// A P for any fine stencil in FP32, for the mixed hierarchies: every output o of the
 // 3 x 3 (x 3) coarse neighbourhood of f (the same ap[o][f] layout as k_ap) is evaluated
 // directly as sum_s A_s(f) wx(g_x - 3 X) wy(g_y - 3 Y) wz(g_z - 3 Z), g = f + d_s, with the
 // linear weights w(t) = 1 - |t|/3 for |t| <= 2. No divergent loops and no shared memory; the
-// 27 x 7 FMAs are cheap on the FP32 pipe (in FP64 they would not be, so the plain method
-// keeps k_ap). Masked fine neighbours and masked coarse nodes contribute nothing.
+// 27 x S FMAs (729 for the 27-point stencil) are cheap on the FP32 pipe (in FP64 they would
+// not be, so the plain method keeps k_ap). Masked fine neighbours and masked coarse nodes
+// contribute nothing.
 __device__ __forceinline__ float lin_w(int t) {
   t = t < 0 ? -t : t;
   return t == 0 ? 1.f : (t == 1 ? 2.f / 3.f : (t == 2 ? 1.f / 3.f : 0.f));

@@ -101,6 +101,9 @@ def lib():
         "rmg_hier_constant_weights": (ctypes.c_int, [P, ctypes.c_int, P]),
         "rmg_hier_convergence_factor": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_ulonglong,
                                                        ctypes.POINTER(ctypes.c_double)]),
+        "rmg_hier_region_energies": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_ulonglong, P, P]),
+        "rmg_hier_blend_weights": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
+        "rmg_hier_region_colours": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "rmg_mlp_num_params": (ctypes.c_int, []),
         "rmg_mlp_create": (ctypes.c_int, [P, P, ctypes.POINTER(P)]),
         "rmg_mlp_destroy": (None, [P]),
@@ -138,6 +141,7 @@ def exported_symbols():
             "rmg_operator_from_block_csr", "rmg_operator_from_host_csr",
             "rmg_hier_dofs_per_node",
             "rmg_hier_opdep_weights", "rmg_hier_constant_weights", "rmg_hier_convergence_factor",
+            "rmg_hier_region_energies", "rmg_hier_blend_weights", "rmg_hier_region_colours",
             "rmg_hier_tile_shape", "rmg_hier_coef_planes", "rmg_hier_galerkin",
             "rmg_mlp_num_params", "rmg_mlp_create",
             "rmg_mlp_destroy", "rmg_mlp_get_params", "rmg_mlp_forward", "rmg_mlp_gradient",
@@ -230,6 +234,7 @@ class Layout:
         self.ctx = ctx
         rd = np.ascontiguousarray(np.asarray(region_dims, dtype=np.int32).reshape(-1))
         self._rd = rd
+        self.nregions = rd.size // 3
         self._keep = (region_gids, dirichlet)
         h = P()
         ctx.check(lib().rmg_layout_create(
@@ -385,6 +390,30 @@ class Hierarchy:
         self.ctx.check(lib().rmg_hier_convergence_factor(self.h, int(iters), int(seed),
                                                          ctypes.byref(v)))
         return v.value
+
+    def region_energies(self, iters=6, seed=7):
+        """(e0, eK): per-region energies e_k^T A^(k) e_k of the error before and after `iters`
+        V-cycles as a stationary solver (numpy arrays, one entry per region)."""
+        nreg = self.layout.nregions
+        e0 = np.zeros(nreg)
+        eK = np.zeros(nreg)
+        self.ctx.check(lib().rmg_hier_region_energies(self.h, int(iters), int(seed),
+                                                      e0.ctypes.data_as(P), eK.ctypes.data_as(P)))
+        return e0, eK
+
+    def blend_weights(self, level, accept, learned, out):
+        """Learned weights at nodes whose regions all accept, linear weights elsewhere."""
+        acc = np.ascontiguousarray(np.asarray(accept, dtype=np.uint8))
+        self.ctx.check(lib().rmg_hier_blend_weights(self.h, level, acc.ctypes.data_as(P),
+                                                    _ptr(learned), _ptr(out)))
+
+    def region_colours(self):
+        """(colours, ncolours): a colouring of the regions in which touching regions differ."""
+        col = np.zeros(self.layout.nregions, dtype=np.int32)
+        nc = ctypes.c_int()
+        self.ctx.check(lib().rmg_hier_region_colours(self.h, col.ctypes.data_as(P),
+                                                     ctypes.byref(nc)))
+        return col, nc.value
 
     def mlp_features(self, level, feats):
         self.ctx.check(lib().rmg_hier_mlp_features(self.h, level, _ptr(feats)))

@@ -40,7 +40,7 @@ def main():
         f.write(f"global_dims {p.global_dims[0]} {p.global_dims[1]} {p.global_dims[2]}\n")
         f.write(f"unknowns {free.size}\n")
         f.write(f"iterations {it}\n")
-        f.write(f"final_relres {hist[-1]!r}\n")
+        f.write(f"final_relres {float(hist[-1])!r}\n")
         f.write(f"norm2 {float(np.linalg.norm(x))!r}\n")
         f.write(f"oracle_seconds {secs:.1f}\n")
         for g in ids:

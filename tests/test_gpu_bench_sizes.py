@@ -111,18 +111,16 @@ def test_fp32_cycle_at_bench_region_sizes(ctx, name):
     assert np.linalg.norm(x.cpu().numpy() - x_or) <= 1e-6 * np.linalg.norm(x_or)
 
 
+
 @pytest.mark.parametrize("name", list(SAMPLES))
 def test_fp32_tile_shapes_identical_at_bench_region_sizes(ctx, name):
-    """Runs, a box shape and the z-marching warp columns (several warps per row of 55- and
-    82-node regions, so the warp-edge fix-ups are exercised) give the same FP32 cycle bit for
-    bit, with the half planes in use."""
+    """Runs and box shapes give the same FP32 cycle bit for bit at the bench's region sizes,
+    with the half planes in use."""
     p, levels, mg = _sample(name)
     ref = None
-    for shape in (0, 8, 9):
+    for shape in (0, 1, 8):
         dp, lay, h = _gpu(ctx, p, 1, shape)
         assert h.coef_planes(0) == (p.stencil + 1) // 2
-        if shape == 9:
-            assert h.tile_shape(0) == (32, 1, 0)
         z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
         h.vcycle(dp.b, z)
         zc = z.cpu().numpy()

@@ -312,3 +312,45 @@ def test_fullsize_pcg_reaches_tolerance_in_each_precision(full):
     for name in ("fp32", "bf16"):
         d = np.linalg.norm(sols[name] - sols["fp64"]) / np.linalg.norm(sols["fp64"])
         print(f"{full.name} {name}: ||x - x_fp64|| / ||x_fp64|| = {d:.3e}")
+
+
+def test_c3_slice_precisions_against_stored_oracle():
+    """Every precision of the 4x4x4-region C3 slice (217^3 nodes, 9.9M unknowns) against the
+    oracle's solution, stored at 4096 sampled unknowns with its full 2-norm by
+    tests/golden/make_c3_slice_oracle.py: the relative RMS difference at the samples estimates
+    ||x - x_oracle|| / ||x_oracle||. Both solutions pass the 1e-10 relative residual test."""
+    import os
+    from paper_2103_11962_gb300 import rmg
+    from workloads import device as WD
+    gold = os.path.join(os.path.dirname(__file__), "golden", "c3_slice_oracle.txt")
+    hdr, ids, vals = {}, [], []
+    for ln in open(gold):
+        if ln.startswith("#"):
+            continue
+        f = ln.split()
+        if f[0].isdigit():
+            ids.append(int(f[0])); vals.append(float(f[1]))
+        else:
+            hdr[f[0]] = f[1:]
+    ids, vals = np.asarray(ids), np.asarray(vals)
+    rms_or = float(hdr["norm2"][0]) / np.sqrt(int(hdr["unknowns"][0]))
+    p = WD.q1_laplace3d(region_grid=(4, 4, 4), n=55, seed=2, device="cuda:0")
+    assert p.n_unknowns == int(hdr["unknowns"][0])
+    ctx = rmg.Context(0)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, torch.from_numpy(p.region_gids).cuda(), p.n_nodes,
+                     torch.from_numpy(p.dirichlet).cuda())
+    lay.operator_from_csr(p.stencil, p.rowptr, p.col, p.val)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    bound = {0: 1e-9, 1: 1e-8, 2: 1e-8}
+    for prec in (0, 1, 2):
+        o = rmg.default_options(levels=4, precision=prec)
+        o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, 1, 1, 3
+        h = rmg.Hierarchy(lay, o)
+        x.zero_()
+        res = h.pcg(p.b, x, rtol=1e-10, maxit=200)
+        assert res["converged"] and res["true_relres"] <= 1e-10
+        xs = x[torch.from_numpy(ids).cuda()].cpu().numpy()
+        err = float(np.sqrt(np.mean((xs - vals) ** 2))) / rms_or
+        print(f"precision {prec}: {res['iterations']} iterations, sampled error {err:.2e}")
+        assert err <= bound[prec], (prec, err)
+        h.close()

@@ -518,3 +518,99 @@ def elasticity3d(region_grid=(3, 3, 3), choices=(28,), seed=4, sigma=0.5, nu=0.3
     return Problem("elasticity3d", 3, 3, gdims, slabs, rdims, gids, mask, A, b, 27,
                    dict(seed=seed, region_grid=tuple(region_grid), choices=tuple(choices),
                         sigma=sigma, nu=nu))
+
+
+# ----------------------------------------------------------------------------------------
+# batches of independent problems
+
+@dataclass
+class Batch:
+    """Independent problems side by side as one system: the composite ids and regions of
+    problem k follow those of problems 0 .. k-1, A is block diagonal, and b, the mask and the
+    region maps are concatenated. The method sees K disconnected components, so one hierarchy
+    (and one V-cycle) treats all of them at once, and quantities summed over the regions of a
+    component belong to that problem alone."""
+
+    name: str
+    dim: int
+    dofs_per_node: int
+    stencil: int
+    region_dims: np.ndarray       # (nregions, 3) int32
+    region_gids: np.ndarray       # (n_r,) int64
+    dirichlet: np.ndarray         # (n_nodes,) uint8
+    A: sp.csr_matrix
+    b: np.ndarray
+    region_component: np.ndarray  # (nregions,) int32: the problem every region belongs to
+    node_offsets: np.ndarray      # (K + 1,) int64: composite id range of every problem
+    members: list = field(default_factory=list)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.dirichlet.shape[0])
+
+    @property
+    def n(self) -> int:
+        return self.n_nodes * self.dofs_per_node
+
+    @property
+    def n_regional_nodes(self) -> int:
+        return int(self.region_gids.shape[0])
+
+    @property
+    def n_unknowns(self) -> int:
+        return int((self.dirichlet == 0).sum()) * self.dofs_per_node
+
+    @property
+    def nregions(self) -> int:
+        return int(self.region_dims.shape[0])
+
+
+def batch(problems) -> Batch:
+    """Concatenate scalar problems of one dimension and stencil into a Batch."""
+    p0 = problems[0]
+    assert all(p.dim == p0.dim and p.stencil == p0.stencil and p.dofs_per_node == 1
+               for p in problems)
+    offs = np.concatenate([[0], np.cumsum([p.n_nodes for p in problems])]).astype(np.int64)
+    gids = np.concatenate([p.region_gids + o for p, o in zip(problems, offs[:-1])])
+    comp = np.concatenate([np.full(p.nregions, k, dtype=np.int32)
+                           for k, p in enumerate(problems)])
+    return Batch(name=f"batch_{p0.name}", dim=p0.dim, dofs_per_node=1, stencil=p0.stencil,
+                 region_dims=np.concatenate([p.region_dims for p in problems]).astype(np.int32),
+                 region_gids=gids.astype(np.int64),
+                 dirichlet=np.concatenate([p.dirichlet for p in problems]).astype(np.uint8),
+                 A=sp.block_diag([p.A for p in problems], format="csr"),
+                 b=np.concatenate([p.b for p in problems]),
+                 region_component=comp, node_offsets=offs, members=list(problems))
+
+
+def highcontrast3d_offset(region_grid=(2, 2, 2), choices=(10,), seed=0, rhs=True,
+                          log10_range=(-3.0, 3.0), blocks=4):
+    """3D 7-point diffusion whose coefficient jumps lie off the coarse-grid planes: kappa is
+    log-uniform in 10^range on a `blocks`^3 grid of boxes whose faces sit at element layers
+    1 or 2 modulo 3 (never on a layer of coarse nodes), so a fine node between two coarse nodes
+    can see a jump inside its interpolation line."""
+    rng = np.random.default_rng(seed)
+    slabs = tuple(tuple(int(v) for v in rng.choice(np.asarray(choices), size=k))
+                  for k in region_grid)
+    gdims, rdims, gids = region_map(slabs)
+    Nx, Ny, Nz = gdims
+    cuts = []
+    for N in (Nx, Ny, Nz):
+        inner = [e for e in range(1, N - 2) if e % 3 != 0]
+        pick = np.sort(rng.choice(np.asarray(inner), size=min(blocks - 1, len(inner)),
+                                  replace=False))
+        cuts.append(np.concatenate([[0], pick, [N - 1]]))
+    kb = 10.0 ** rng.uniform(log10_range[0], log10_range[1],
+                             size=(len(cuts[2]) - 1, len(cuts[1]) - 1, len(cuts[0]) - 1))
+    kappa = np.empty((Nz - 1, Ny - 1, Nx - 1))
+    for c in range(len(cuts[2]) - 1):
+        for bb in range(len(cuts[1]) - 1):
+            for a in range(len(cuts[0]) - 1):
+                kappa[cuts[2][c]:cuts[2][c + 1], cuts[1][bb]:cuts[1][bb + 1],
+                      cuts[0][a]:cuts[0][a + 1]] = kb[c, bb, a]
+    mask = boundary_mask(gdims)
+    A = diffusion3d_7pt_from_kappa(gdims, kappa, mask)
+    b = _rhs(rng, A.shape[0], mask) if rhs else np.zeros(A.shape[0])
+    return Problem("highcontrast3d_offset", 3, 1, gdims, slabs, rdims, gids, mask, A, b, 7,
+                   dict(seed=seed, region_grid=tuple(region_grid), choices=tuple(choices),
+                        cuts=[c.tolist() for c in cuts], kappa_block=kb))
