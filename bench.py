@@ -716,7 +716,7 @@ def learned_leg(B, wl, family, n_train, K, W_, prec="fp32"):
                                             device=B.dev, batch=50)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    net, hist = learned.train(B.ctx, F, Y, M, steps=2000, batch=16384, lr=2e-3)
+    net, hist = learned.train(B.ctx, F, Y, M, steps=8000, batch=16384, lr=2e-3)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out = {"family": family, "train_operators": n_train, "samples": int(F.shape[0]),

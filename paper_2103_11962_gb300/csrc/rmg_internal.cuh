@@ -188,6 +188,7 @@ struct Level {
   DBuf<int> gslot;               // regional slots of every group, ascending
   DBuf<int> rid;                 // region of every regional node (built for the split)
   DBuf<int> sgrp;                // group of every group slot (nslots)
+  DBuf<int4> affine;             // per region {g0, gy, gz, ok}: gid = g0 + i + gy j + gz l
   // operator
   DBuf<double> coef;             // kind * n_r, slot-major
   DBuf<double> dinv;             // 1 / (Psi^T Psi diag([[A]]))

@@ -147,35 +147,7 @@ __device__ __forceinline__ float stencil_row_half(const float* __restrict__ half
   static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
   constexpr int C = S::CENTER;
   const int sy = R.nx, sz = R.nx * R.ny;
-#ifndef RMG_HALF_GATHER
-#define RMG_HALF_GATHER 1
-#endif
-  if constexpr (!(RMG_HALF_GATHER && S::S >= 9)) {
-    // 5/7-point rows: load and multiply slot by slot (the compiler keeps them at 32 registers)
-    float au = 0.f;
-#pragma unroll
-    for (int s = 0; s < S::S; ++s) {
-      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
-      bool ok = true;
-      if (dx < 0) ok &= (i > 0);
-      if (dx > 0) ok &= (i < R.nx - 1);
-      if (dy < 0) ok &= (j > 0);
-      if (dy > 0) ok &= (j < R.ny - 1);
-      if (dz < 0) ok &= (l > 0);
-      if (dz > 0) ok &= (l < R.nz - 1);
-      if (ok) {
-        const int nb = n + dx + dy * sy + dz * sz;
-        const float c = s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
-                              : half[(size_t)(s - C) * (size_t)n_r + n];
-        au = fmaf(c, u[nb], au);
-      }
-    }
-    return au;
-  } else {
-  // 9/27-point rows: all coefficient and neighbour loads of the row first (independent, so
-  // they are in flight together), then the products in slot order
-  float cv[S::S], uv[S::S];
-  bool okv[S::S];
+  float au = 0.f;
 #pragma unroll
   for (int s = 0; s < S::S; ++s) {
     const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
@@ -186,19 +158,14 @@ __device__ __forceinline__ float stencil_row_half(const float* __restrict__ half
     if (dy > 0) ok &= (j < R.ny - 1);
     if (dz < 0) ok &= (l > 0);
     if (dz > 0) ok &= (l < R.nz - 1);
-    okv[s] = ok;
-    const int nb = n + dx + dy * sy + dz * sz;
-    cv[s] = ok ? (s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
-                        : half[(size_t)(s - C) * (size_t)n_r + n])
-               : 0.f;
-    uv[s] = ok ? u[nb] : 0.f;
+    if (ok) {
+      const int nb = n + dx + dy * sy + dz * sz;
+      const float c = s < C ? half[(size_t)(S::S - 1 - s - C) * (size_t)n_r + nb]
+                            : half[(size_t)(s - C) * (size_t)n_r + n];
+      au = fmaf(c, u[nb], au);
+    }
   }
-  float au = 0.f;
-#pragma unroll
-  for (int s = 0; s < S::S; ++s)
-    if (okv[s]) au = fmaf(cv[s], uv[s], au);
   return au;
-  }
 }
 
 // Half planes of a float stencil; *asym becomes 1 when a mirrored pair inside a region differs

@@ -188,7 +188,52 @@ __global__ void k_group_sort(int ngroups, const int* __restrict__ gptr, int* __r
 __global__ void k_fill_int(int n, int* p, int v) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
 }
+
+// Candidate affine gid map of every region, gid(i, j, l) = g0 + i + gy j + gz l, read off the
+// nodes (1,0,0), (0,1,0) and (0,0,1). It is kept (w = 1) only when the split can invert it by
+// comparisons: gy >= 3 and, in 3D, gz >= 2 gy + 3 (see box_offset_affine); 2D regions take
+// gz = 2^30, which no column offset reaches.
+__global__ void k_affine_init(int nreg, int dim, const RegionDev* __restrict__ regions,
+                              const int* __restrict__ gid, int4* __restrict__ aff) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+    const RegionDev R = regions[r];
+    int4 a = make_int4(0, 0, 0, 0);
+    bool ok = R.nx >= 2 && R.ny >= 2 && (dim == 2 ? R.nz == 1 : R.nz >= 2);
+    if (ok) {
+      a.x = gid[R.off];
+      ok = gid[R.off + 1] - a.x == 1;
+      a.y = gid[R.off + R.nx] - a.x;
+      a.z = dim == 2 ? (1 << 30) : gid[R.off + R.nx * R.ny] - a.x;
+      ok = ok && a.y >= 3 && (dim == 2 || (a.z >= 2 * a.y + 3 && a.z < (1 << 29)));
+    }
+    a.w = ok ? 1 : 0;
+    aff[r] = a;
+  }
+}
+
+// Clears the flag of a region with any node off its candidate map.
+__global__ void k_affine_check(Grid G, const int* __restrict__ gid, int4* __restrict__ aff) {
+  RMG_FOR_NODES(G)
+    const int4 a = aff[tile_.region];
+    if (!a.w) continue;
+    int i, j, l;
+    decode(li, R, i, j, l);
+    const long long want = (long long)a.x + i + (long long)a.y * j + (long long)a.z * l;
+    if (want != (long long)gid[n]) aff[tile_.region].w = 0;   // every writer stores 0
+  RMG_END_FOR_NODES
+}
 }  // namespace
+
+// Affine gid maps of the regions of a level (Level::affine), for the split's shortcut.
+void build_affine(Ctx& c, Level& L) {
+  L.affine.alloc(L.nreg);
+  k_affine_init<<<persistent_grid(c, (L.nreg + 255) / 256), 256, 0, c.stream>>>(
+      L.nreg, L.dim, L.regions.get(), L.gid.get(), L.affine.get());
+  RMG_LAUNCHED();
+  k_affine_check<<<persistent_grid(c, (int)L.htiles.size()), kTile, 0, c.stream>>>(
+      L.grid(), L.gid.get(), L.affine.get());
+  RMG_LAUNCHED();
+}
 
 void build_tiles(Level& L) {
   L.htiles.clear();
@@ -291,6 +336,7 @@ void layout_create(Ctx& c, Level& L, int dim, int nreg, const int* dims, const i
       L.n_r, g64, ncomp, L.gid.get(), count.get(), c.d_err.get());
   RMG_LAUNCHED();
   build_groups(c, L, dir, nullptr, count);
+  build_affine(c, L);
   c.check_device_error("rmg_layout_create");
 }
 
@@ -343,6 +389,28 @@ __device__ __forceinline__ void box_offset(int d, int sy, int sz, int& dx, int& 
   dx = d;
 }
 
+// The same for a composite column offset d = c - g = dx + gy dy + gz dz of an affine region
+// (gy >= 3, gz >= 2 gy + 3). d comes from an unchecked column, so the comparisons halve the
+// strides instead of doubling d (2 d > s <=> d > floor(s / 2) for integers), and dx is clamped
+// to [-2, 2]: an offset outside the 3x3x3 box comes out with |dx| > 1 or lands on the wrong
+// node, which the caller rules out (affine_holds).
+__device__ __forceinline__ void box_offset_affine(int d, int gy, int gz, int& dx, int& dy,
+                                                  int& dz) {
+  dz = 0;
+  if (d > (gz >> 1)) { dz = 1; d -= gz; } else if (-d > (gz >> 1)) { dz = -1; d += gz; }
+  dy = 0;
+  if (d > (gy >> 1)) { dy = 1; d -= gy; } else if (-d > (gy >> 1)) { dy = -1; d += gy; }
+  dx = d > 2 ? 2 : (d < -2 ? -2 : d);
+}
+
+// Whether composite node c (0 <= c < 2^31) is a node of affine region R (a: its map).
+__device__ __forceinline__ bool affine_holds(int c, const int4& a, const RegionDev& R) {
+  const int rel = c - a.x;                     // a.x >= 0: no overflow
+  if (rel < 0) return false;
+  const int l = rel / a.z, rem = rel - l * a.z, j = rem / a.y, i = rem - j * a.y;
+  return l < R.nz && j < R.ny && i < R.nx;
+}
+
 // One regional node per thread and one row component c per blockIdx.y: the thread scans the
 // CSR row g * B + c once and writes every entry straight into its coefficient stream
 // coef[((c * B + c') * S + slot) * n_r + n] (threads of a warp are consecutive nodes, so for
@@ -365,7 +433,8 @@ __global__ void RMG_SPLIT_BOUNDS
 k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
             const int* __restrict__ c2r, const int* __restrict__ cgrp,
             const int* __restrict__ gptr, const int* __restrict__ gslot,
-            const int* __restrict__ rid, const int64_t* __restrict__ rowptr,
+            const int* __restrict__ rid, const int4* __restrict__ affine,
+            const int64_t* __restrict__ rowptr,
             const int64_t* __restrict__ col, const double* __restrict__ val, int ncomp,
             double* __restrict__ coef, int* err) {
   using S = Sten<KIND>;
@@ -378,6 +447,10 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
     const bool peel = R.nx >= 3 && R.ny >= 3;    // box_offset is exact
     const int g = gid[n];
     const bool shared = mult[n] > 1;
+    // rows of single-copy nodes of a region whose gid map is affine (k_affine_*) find the slot
+    // of every entry from c - g alone, without the composite-indexed gathers
+    const int4 af = affine[tile_.region];
+    const bool fast = af.w != 0 && !shared;
     double zsum[B], offsum[B];
     unsigned seen[B];                            // slots already written (27 < 32 bits)
 #pragma unroll
@@ -411,7 +484,7 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
           cp[u] = (int)(c64 - (int64_t)c * B);
         }
         cn[u] = c;
-        if (c != g) grp[u] = cgrp[c];
+        if (c != g && !fast) grp[u] = cgrp[c];
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -421,25 +494,39 @@ k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mul
         const double v = vv[u];
         zsum[b] += v;
         if (c == g) continue;
-        // regional slot of c inside this region (its group was loaded above)
-        int sc = -1;
-        if (grp[u] < 0) {
-          const int s0 = c2r[c];
-          sc = (s0 >= R.off && s0 < R.off + nodes) ? s0 : -1;
-        } else {
-          for (int q = gptr[grp[u]]; q < gptr[grp[u] + 1]; ++q) {
-            const int s0 = gslot[q];
-            if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
-          }
-        }
-        if (sc < 0) continue;                      // entry belongs to other regions only
         int dx, dy, dz;
-        if (peel) {
-          box_offset(sc - n, sy, sz, dx, dy, dz);
+        if (fast) {
+          // c = g + dx + gy dy + gz dz inside the 3x3x3 box: when that position lies in the
+          // region, c is the node there (the map is affine over the region). Any other column
+          // is a node of this region (outside the stencil: the error below, as on the general
+          // path) or of other regions only (skipped, as there).
+          box_offset_affine(c - g, af.y, af.z, dx, dy, dz);
+          const bool in_region = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
+                                 j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
+          if (!in_region) {
+            if (affine_holds(c, af, R)) set_err(err, DERR_STENCIL);
+            continue;
+          }
         } else {
-          int ic, jc, lc;
-          decode(sc - R.off, R, ic, jc, lc);
-          dx = ic - i; dy = jc - j; dz = lc - l;
+          // regional slot of c inside this region (its group was loaded above)
+          int sc = -1;
+          if (grp[u] < 0) {
+            const int s0 = c2r[c];
+            sc = (s0 >= R.off && s0 < R.off + nodes) ? s0 : -1;
+          } else {
+            for (int q = gptr[grp[u]]; q < gptr[grp[u] + 1]; ++q) {
+              const int s0 = gslot[q];
+              if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
+            }
+          }
+          if (sc < 0) continue;                    // entry belongs to other regions only
+          if (peel) {
+            box_offset(sc - n, sy, sz, dx, dy, dz);
+          } else {
+            int ic, jc, lc;
+            decode(sc - R.off, R, ic, jc, lc);
+            dx = ic - i; dy = jc - j; dz = lc - l;
+          }
         }
         const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
                             j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
@@ -513,12 +600,13 @@ void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, co
     k_region_ids<<<persistent_grid(c, G.ntiles), kTile, 0, c.stream>>>(G, L.rid.get());
     RMG_LAUNCHED();
   }
+  if (L.affine.n < (size_t)L.nreg) build_affine(c, L);
   const dim3 gb(persistent_grid(c, G.ntiles), B);
 #define RMG_SPLIT(K, BB)                                                                    \
   k_split_csr<K, BB><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(), \
                                                  L.cgrp.get(), L.gptr.get(), L.gslot.get(),  \
-                                                 L.rid.get(), rowptr, col, val, L.ncomp,     \
-                                                 L.coef.get(), c.d_err.get())
+                                                 L.rid.get(), L.affine.get(), rowptr, col,   \
+                                                 val, L.ncomp, L.coef.get(), c.d_err.get())
   switch (kind) {
     case 5: RMG_SPLIT(5, 1); break;
     case 7: RMG_SPLIT(7, 1); break;

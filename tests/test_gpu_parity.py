@@ -125,6 +125,43 @@ def test_host_csr_split_matches_device_csr(ctx, name):
         lay.operator_from_host_csr(p.stencil, 2, *host)
 
 
+@pytest.mark.parametrize("name", ["diff3d_small", "q1_3d_small", "q1_2d"])
+def test_split_without_affine_numbering(ctx, name):
+    """The split takes a shortcut for single-copy rows of regions whose composite ids are
+    numbered lexicographically (an affine gid map). Renumbering the composite nodes at random
+    (rows and columns of A, gids and Dirichlet flags alike, entries kept in their row order)
+    leaves no region affine, so every row takes the general path: the region stencils must be
+    the same bit for bit."""
+    from paper_2103_11962_gb300 import rmg, upload
+    p, _ = _problem(name)
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    h = rmg.Hierarchy(lay, rmg.default_options(levels=2))
+    n_r, _, kind = h.level_sizes(0)
+    ref = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
+    h.level_export(0, coeffs=ref)
+    A = p.A.tocsr()
+    perm = np.random.default_rng(3).permutation(p.n_nodes)        # old id -> new id
+    inv = np.argsort(perm)                                         # new id -> old id
+    counts = np.diff(A.indptr)[inv]
+    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    take = np.concatenate([np.arange(A.indptr[g], A.indptr[g + 1]) for g in inv])
+    col = perm[A.indices[take]].astype(np.int64)
+    val = A.data[take].astype(np.float64)
+    gids = torch.from_numpy(perm[np.asarray(p.region_gids)].astype(np.int64)).cuda()
+    dirn = np.zeros(p.n_nodes, dtype=np.uint8)
+    dirn[perm] = np.asarray(p.dirichlet, dtype=np.uint8)
+    lay2 = rmg.Layout(ctx, p.dim, p.region_dims, gids, p.n_nodes, torch.from_numpy(dirn).cuda())
+    lay2.operator_from_csr(p.stencil, torch.from_numpy(rowptr).cuda(),
+                           torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda())
+    h2 = rmg.Hierarchy(lay2, rmg.default_options(levels=2))
+    got = torch.empty_like(ref)
+    h2.level_export(0, coeffs=got)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_regional_apply_equals_composite(ctx, name):
     """Psi^T Psi [[A]] Psi^T x = Psi^T (A x) on the GPU (eq. regional residual)."""
