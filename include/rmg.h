@@ -95,10 +95,14 @@ typedef struct {
  * launch covers all regions of a level with blocks of 256 threads, each block one tile of one
  * region. Shape 0: runs of 256 consecutive regional nodes. Shapes 1..8: boxes tx x ty x tz of
  * (32,8,1), (64,4,1), (128,2,1), (16,16,1), (32,4,2), (16,8,2), (16,4,4), (8,8,4); in 2D only
- * the tz = 1 boxes apply. With -1 the first numeric setup times every applicable shape on
- * every smoothed level (the residual sweep in the hierarchy's precision, CUDA events) and keeps
- * the fastest; the choice does not change any result (each node computes the same row). */
-#define RMG_NUM_TILE_SHAPES 9
+ * the tz = 1 boxes apply. Shape 9: 32 x 8 tiles of a region's x-y planes, each block stepping
+ * through all z-planes with the tile (and a one-node ring) of u and of the coefficient planes
+ * copied into shared memory ahead of use; it applies to the half-plane sweeps of a 3D 27-point
+ * level 0 in the FP32 cycle (rmg_hier_tile_shape reports 32 x 8 x 0). With -1 the first
+ * numeric setup times every applicable shape on every smoothed level (the residual sweep in
+ * the hierarchy's precision, CUDA events) and keeps the fastest; the choice does not change any
+ * result (each node computes the same row). */
+#define RMG_NUM_TILE_SHAPES 10
 
 typedef struct {
   int iterations;        /* products with A (0 when the initial residual already passes)  */

@@ -1179,14 +1179,23 @@ static void make_low_precision(Hier& h) {
 
 // ---------------------------------------------------------------------- tile-shape autotuner
 // Candidate tile shapes of the stencil sweeps: index 0 = runs of kTile consecutive nodes,
-// 1.. = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty). Boxes hand every
-// thread its (i, j, l) without a decode and keep stencil neighbours inside the block, at the
-// price of idle threads where a box overhangs the region; which wins depends on the region
-// sizes, the stencil and the precision, so each hierarchy times them.
+// 1..8 = boxes tx x ty x tz (tx * ty * tz = kTile, given as log2 tx, log2 ty), 9 = 32 x 8
+// columns staged through shared memory (27-point FP32 half planes). Boxes hand every thread
+// its (i, j, l) without a decode and keep stencil neighbours inside the block, at the price of
+// idle threads where a box overhangs the region; which wins depends on the region sizes, the
+// stencil and the precision, so each hierarchy times them.
 
 static bool shape_fits(const Hier& h, int l, int k) {
   const Level& L = *h.lv[l];
   const TileShape t = kTileShapes[k];
+  if (k == kStagedShape) {     // FP32 half-plane sweeps of a 3D 27-point scalar stencil only
+    if (!(h.half(l) != nullptr && L.B == 1 && L.dim == 3 && L.kind == 27 &&
+          h.o.smoother != RMG_SMOOTHER_GS))
+      return false;
+    for (int d : L.hdims)
+      if (d >= 32768) return false;                       // tile corners are 16-bit
+    return true;
+  }
   if (t.lx < 0) return true;
   if (L.dim == 2 && t.lx + t.ly != 8) return false;      // 2D levels need tz = 1
   for (int d : L.hdims)
@@ -1198,13 +1207,22 @@ static void set_shape(Hier& h, int l, int k) {
   Level& L = *h.lv[l];
   h.shape[l] = k;
   const TileShape t = kTileShapes[k];
-  if (t.lx < 0) {
+  if (t.lx == -1) {
     h.sgrid[l] = L.grid();
     return;
   }
-  const int tx = 1 << t.lx, ty = 1 << t.ly, tz = kTile >> (t.lx + t.ly);
   std::vector<Tile> tl;
-  for (int r = 0; r < L.nreg; ++r) {
+  if (t.lx == -3) {
+    // staged columns: one 32 x 8 tile of the x-y planes per block, through all z-planes
+    for (int r = 0; r < L.nreg; ++r) {
+      const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1];
+      for (int y = 0; y < ny; y += kStY)
+        for (int x = 0; x < nx; x += kStX) tl.push_back(Tile{r, 0, (short)x, (short)y, 0, 0});
+    }
+  }
+  const int tx = t.lx < 0 ? 1 : 1 << t.lx, ty = t.lx < 0 ? 1 : 1 << t.ly;
+  const int tz = t.lx < 0 ? 1 : kTile >> (t.lx + t.ly);
+  for (int r = 0; r < L.nreg && t.lx >= 0; ++r) {
     const int nx = L.hdims[3 * r], ny = L.hdims[3 * r + 1], nz = L.hdims[3 * r + 2];
     for (int z = 0; z < nz; z += tz)
       for (int y = 0; y < ny; y += ty)
@@ -1278,6 +1296,10 @@ static void autotune(Hier& h) {
 }
 
 void tile_shape(const Hier& h, int l, int* tx, int* ty, int* tz) {
+  if (h.shape[l] == kStagedShape) {
+    *tx = kStX; *ty = kStY; *tz = 0;
+    return;
+  }
   const TileShape t = kTileShapes[h.shape[l]];
   *tx = t.lx < 0 ? 0 : 1 << t.lx;
   *ty = t.lx < 0 ? 0 : 1 << t.ly;

@@ -16,11 +16,14 @@ struct LevelVecs {
   }
 };
 
-// Stencil-sweep tile shapes (index 0: runs of kTile consecutive nodes; 1..: boxes
-// 2^lx x 2^ly x kTile / 2^(lx + ly)), in the order rmg_options.tile_shape numbers them.
+// Stencil-sweep tile shapes (index 0: runs of kTile consecutive nodes; 1..8: boxes
+// 2^lx x 2^ly x kTile / 2^(lx + ly); 9: 32 x 8 columns through all z-planes of a region,
+// staged in shared memory (k_stencil_half27_staged), marked lx = -3), in the order
+// rmg_options.tile_shape numbers them.
 struct TileShape { int lx, ly; };
 constexpr TileShape kTileShapes[] = {{-1, 0}, {5, 3}, {6, 2}, {7, 1}, {4, 4},
-                                     {5, 2}, {4, 3}, {4, 2}, {3, 3}};
+                                     {5, 2}, {4, 3}, {4, 2}, {3, 3}, {-3, 0}};
+constexpr int kStagedShape = 9;
 constexpr int kNumTileShapes = (int)(sizeof(kTileShapes) / sizeof(kTileShapes[0]));
 static_assert(kNumTileShapes == RMG_NUM_TILE_SHAPES, "tile shape table and header disagree");
 

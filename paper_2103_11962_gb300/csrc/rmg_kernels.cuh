@@ -236,6 +236,171 @@ k_stencil_half(Grid G, const float* __restrict__ coef, const float* __restrict__
   else stencil_pass<true, KIND>(G, half, u, mult, y, epi);
 }
 
+// ---- staged 27-point half-plane sweep: region tiles in shared memory, pipelined ----------
+// A block owns a kStX x kStY tile of the x-y planes of one region (tiles[t] = {region, -, x0,
+// y0}) and steps through all z-planes of the region. For plane l it needs u of planes l-1..l+1
+// and the 14 half planes of planes l-1 and l (the own coefficients of plane l; the mirrored
+// coefficients of the in-plane neighbours, half planes 1..4, and of the neighbours below, half
+// planes 5..13), each with a one-node ring around the tile. Every row of such a window (34
+// nodes) is copied from global to shared memory with 16-byte cp.async, starting at the 16-byte
+// boundary at or below the row's first node, into 40-float shared rows; a row's nodes start
+// at the offset m = (element index of its first node) mod 4 of that row. Region rows need not
+// be aligned: only the array bases must be (checked at launch). While the block computes plane
+// l, the copies of the coefficients of planes up to l + kStAhead and of u up to l + 1 +
+// kStAhead are in flight. Each node forms the products of stencil_row_half in the same slot
+// order, so its row is bit for bit that of the other shapes.
+#ifndef RMG_ST_AHEAD
+#define RMG_ST_AHEAD 1
+#endif
+constexpr int kStX = 32, kStY = 8;
+constexpr int kStRows = kStY + 2, kStRow = 40;           // window rows with the ring; floats
+constexpr int kStPlane = kStRows * kStRow;               // one staged plane
+constexpr int kStAhead = RMG_ST_AHEAD;                   // planes copied ahead of use
+constexpr int kStCoef = kStAhead + 2, kStU = kStAhead + 3;   // ring depths
+constexpr int kStSmemFloats = (kStCoef * 14 + kStU) * kStPlane;
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy the windows of planes [0, np) of `src` (plane stride n_r, src 16-byte aligned, `total`
+// floats long) at z-plane l of region R, tile corner (x0, y0), into dst[p][row][0..40). Only
+// 16-byte chunks that hold a node of the region are copied; a chunk that would end past the
+// array goes element by element. Other shared words keep stale values and are never read.
+__device__ __forceinline__ void stage_windows(float* dst, const float* __restrict__ src, int np,
+                                              long long n_r, long long total,
+                                              const RegionDev& R, int x0, int y0, int l) {
+  constexpr int kChunks = kStRow / 4;
+  const int chunks = np * kStRows * kChunks;
+  const int lo_cx = x0 == 0 ? 1 : 0, hi_cx = min(kStX + 1, R.nx - x0);
+  for (int e = threadIdx.x; e < chunks; e += blockDim.x) {
+    const int p = e / (kStRows * kChunks), rem = e - p * (kStRows * kChunks);
+    const int row = rem / kChunks, k = rem - row * kChunks;
+    const int j = y0 + row - 1;
+    if (j < 0 || j >= R.ny) continue;
+    const long long gs = (long long)p * n_r + R.off +
+                         (long long)R.nx * (j + (long long)R.ny * l) + x0 - 1;   // node cx = 0
+    const long long c = (gs & ~3LL) + 4 * k;
+    if (c + 3 < gs + lo_cx || c > gs + hi_cx) continue;
+    float* d = dst + p * kStPlane + row * kStRow + 4 * k;
+    if (c + 4 <= total) {
+      cp_async16(d, src + c);
+    } else {
+      for (int q = 0; q < 4 && c + q < total; ++q) cp_async4(d + q, src + c + q);
+    }
+  }
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(kStX * kStY)
+k_stencil_half27_staged(Grid G, const float* __restrict__ coef, const float* __restrict__ half,
+                        const int* __restrict__ asym, const float* __restrict__ u,
+                        const uint8_t* __restrict__ mult, float* __restrict__ y, Epi epi) {
+  extern __shared__ __align__(16) float st_smem[];
+  float* CS = st_smem;                                // [kStCoef][14][kStPlane]
+  float* US = st_smem + kStCoef * 14 * kStPlane;      // [kStU][kStPlane]
+  const int tx = threadIdx.x % kStX, ty = threadIdx.x / kStX;
+  const bool full = *asym != 0;
+  const long long n_r = G.n_r;
+  const unsigned nr3 = (unsigned)G.n_r & 3u;
+  for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) {
+    const Tile tile = G.tiles[t];
+    const RegionDev R = G.regions[tile.region];
+    const int x0 = tile.x0, y0 = tile.y0;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool in = i < R.nx && j < R.ny;
+    if (full) {                                       // asymmetric operator: full planes
+      for (int l = 0; l < R.nz && in; ++l) {
+        const int n = R.off + i + R.nx * (j + R.ny * l);
+        const float au = stencil_row<27, float, float, float>(coef, u, n, G.n_r, i, j, l, R);
+        if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
+      }
+      continue;
+    }
+    // prologue: u planes 0 .. kStAhead and the coefficients of planes 0 .. kStAhead - 1, one
+    // group per plane (u plane 0 joins the first)
+    for (int q = 0; q < kStAhead; ++q) {
+      if (q == 0) stage_windows(US, u, 1, n_r, n_r, R, x0, y0, 0);
+      if (q + 1 < R.nz)
+        stage_windows(US + ((q + 1) % kStU) * kStPlane, u, 1, n_r, n_r, R, x0, y0, q + 1);
+      if (q < R.nz)
+        stage_windows(CS + (q % kStCoef) * 14 * kStPlane, half, 14, n_r, 14 * n_r, R, x0, y0, q);
+      cp_async_commit();
+    }
+    // m of window row ty + ri at z-plane z: (off + x0 - 1 + nx (y0 - 1 + ty + ri + ny z)) mod 4;
+    // half plane q adds q n_r
+    const unsigned cst = (unsigned)(R.off + x0 - 1) + (unsigned)R.nx * (unsigned)(y0 - 1 + ty);
+    const bool xm = i > 0, xp = i < R.nx - 1, ym = j > 0, yp = j < R.ny - 1;
+    for (int l = 0; l < R.nz; ++l) {
+      // copies for later planes: coefficients of l + kStAhead, u of l + 1 + kStAhead
+      const int lc = l + kStAhead, lu = l + 1 + kStAhead;
+      if (lc < R.nz)
+        stage_windows(CS + (lc % kStCoef) * 14 * kStPlane, half, 14, n_r, 14 * n_r, R, x0, y0, lc);
+      if (lu < R.nz) stage_windows(US + (lu % kStU) * kStPlane, u, 1, n_r, n_r, R, x0, y0, lu);
+      cp_async_commit();
+      cp_async_wait<kStAhead>();                      // the groups of planes <= l have landed
+      __syncthreads();
+      if (in) {
+        const bool zm = l > 0, zp = l < R.nz - 1;
+        const float* Cc = CS + (l % kStCoef) * 14 * kStPlane;                    // plane l
+        const float* Cp = CS + ((l + kStCoef - 1) % kStCoef) * 14 * kStPlane;    // plane l - 1
+        const float* Uz[3] = {US + ((l + kStU - 1) % kStU) * kStPlane, US + (l % kStU) * kStPlane,
+                              US + ((l + 1) % kStU) * kStPlane};
+        unsigned m[3][3];                              // [z-plane l-1..l+1][window row ty..ty+2]
+#pragma unroll
+        for (int zi = 0; zi < 3; ++zi)
+#pragma unroll
+          for (int ri = 0; ri < 3; ++ri)
+            m[zi][ri] = (cst + (unsigned)R.nx * (unsigned)(ri + R.ny * (l - 1 + zi))) & 3u;
+        float au = 0.f;
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+          const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+          bool ok = true;
+          if (dx < 0) ok &= xm;
+          if (dx > 0) ok &= xp;
+          if (dy < 0) ok &= ym;
+          if (dy > 0) ok &= yp;
+          if (dz < 0) ok &= zm;
+          if (dz > 0) ok &= zp;
+          if (ok) {
+            const int cell = (ty + 1 + dy) * kStRow + tx + 1 + dx;
+            float c;
+            if (s < 13) {                              // mirror slot, at the neighbour
+              const int q = 13 - s;
+              const unsigned mq = (q * nr3 + m[dz + 1][dy + 1]) & 3u;
+              c = (dz < 0 ? Cp : Cc)[q * kStPlane + cell + mq];
+            } else {                                   // own slot
+              const int q = s - 13;
+              const unsigned mq = (q * nr3 + m[1][1]) & 3u;
+              c = Cc[q * kStPlane + (ty + 1) * kStRow + tx + 1 + mq];
+            }
+            const float v = Uz[dz + 1][cell + m[dz + 1][dy + 1]];
+            au = fmaf(c, v, au);
+          }
+        }
+        const int n = R.off + i + R.nx * (j + R.ny * l);
+        if (mult[n] > 1) y[n] = au; else epi(n, au, 1);
+      }
+      __syncthreads();                                // before the rings are overwritten
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+}
+
 // Phase B: interface groups. y holds the partial row results of every copy. One thread per
 // copy: it sums the partial results of its group in ascending slot order (every copy of a group
 // forms the identical sum) and applies the epilogue to its own copy.

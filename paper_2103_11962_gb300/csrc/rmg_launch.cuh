@@ -3,6 +3,8 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdint>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
@@ -32,6 +34,29 @@ inline int resident_per_sm(const void* kernel) {
   return b;
 }
 
+// The same for a kernel with `smem` bytes of dynamic shared memory; also raises the kernel's
+// dynamic shared memory limit, once per device (the attribute belongs to the device's context).
+inline int resident_per_sm_smem(const void* kernel, int smem) {
+  static std::mutex m;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  RMG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  const auto key = std::make_pair(kernel, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kTile, smem) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  b = std::max(1, std::min(b, 8));
+  cache.emplace(key, b);
+  return b;
+}
+
 // kernel<<<one resident wave of blocks over `work` tiles, kTile>>>(args...) on st.
 template <typename... P, typename... A>
 void launch_resident(const Ctx& c, void (*kernel)(P...), int work, cudaStream_t st,
@@ -57,14 +82,26 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
                     cudaStream_t st, int* launches, cudaEvent_t ev0 = nullptr,
                     cudaEvent_t ev1 = nullptr, const Grid* sweep = nullptr,
                     const float* half = nullptr, const int* asym = nullptr) {
-  const Grid G = sweep ? *sweep : L.grid();
+  Grid G = sweep ? *sweep : L.grid();
+  // staged tiles copy 16-byte chunks: with an unaligned u or half-plane array the level's run
+  // tiles take over
+  if (G.lx == -3 && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(half)) & 15))
+    G = L.grid();
   const int gb = persistent_grid(c, G.ntiles);
   // external record nodes when capturing, so the events can be timed after a graph replay
   if (ev0) RMG_CUDA(cudaEventRecordWithFlags(ev0, st, g_capturing ? cudaEventRecordExternal : 0));
   bool done = false;
   if constexpr (std::is_same<CT, float>::value && std::is_same<VT, float>::value &&
                 std::is_same<AT, float>::value) {
-    if (half && L.B == 1) {
+    if (half && L.B == 1 && G.lx == -3) {
+      RMG_REQUIRE(asym != nullptr && L.kind == 27, RMG_ERR_STATE,
+                  "staged sweeps need the half planes of a 27-point stencil");
+      const int smem = kStSmemFloats * (int)sizeof(float);
+      const auto kern = k_stencil_half27_staged<Epi>;
+      const int g = persistent_grid(c, G.ntiles, resident_per_sm_smem((const void*)kern, smem));
+      kern<<<g, kStX * kStY, smem, st>>>(G, coef, half, asym, u, L.mult.get(), y, epi);
+      done = true;
+    } else if (half && L.B == 1) {
       RMG_REQUIRE(asym != nullptr, RMG_ERR_STATE, "half planes without their flag");
       const int nt = G.ntiles;
       const uint8_t* mu = L.mult.get();
@@ -77,6 +114,7 @@ void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, 
       done = true;
     }
   }
+  RMG_REQUIRE(done || G.lx != -3, RMG_ERR_STATE, "staged tiles outside a half-plane sweep");
   if (done) {
   } else if (L.B == 1) {
     switch (L.kind) {

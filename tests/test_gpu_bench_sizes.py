@@ -114,13 +114,15 @@ def test_fp32_cycle_at_bench_region_sizes(ctx, name):
 
 @pytest.mark.parametrize("name", list(SAMPLES))
 def test_fp32_tile_shapes_identical_at_bench_region_sizes(ctx, name):
-    """Runs and box shapes give the same FP32 cycle bit for bit at the bench's region sizes,
-    with the half planes in use."""
+    """Runs, box shapes and (27-point) the shared-memory staged columns give the same FP32
+    cycle bit for bit at the bench's region sizes, with the half planes in use."""
     p, levels, mg = _sample(name)
     ref = None
-    for shape in (0, 1, 8):
+    for shape in (0, 1, 8, 9):
         dp, lay, h = _gpu(ctx, p, 1, shape)
         assert h.coef_planes(0) == (p.stencil + 1) // 2
+        if shape == 9:
+            assert h.tile_shape(0) == ((32, 8, 0) if p.stencil == 27 else (0, 0, 0))
         z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
         h.vcycle(dp.b, z)
         zc = z.cpu().numpy()

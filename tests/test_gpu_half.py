@@ -134,3 +134,34 @@ def test_coef_planes_of_other_precisions(ctx):
         assert h.coef_planes(0) == 7 and h.coef_planes(1) == 27
         with pytest.raises(Exception):
             h.coef_planes(nlev)
+
+
+@pytest.mark.parametrize("perturb", [False, True])
+def test_staged_sweep_matches_full_planes(ctx, perturb):
+    """Tile shape 9 (27-point half planes staged through shared memory) against run tiles on
+    the full planes: bitwise the same cycle for a symmetric operator, and for one whose FP32
+    pairs differ (the staged kernel then reads the full planes itself)."""
+    from paper_2103_11962_gb300 import rmg, upload
+    p, nlev = _problem("q1_3d_small")
+    dp = upload(p)
+    if perturb:
+        A = _perturbed(p)
+        dp.val = torch.from_numpy(A.data.astype(np.float64)).cuda()
+        dp.rowptr = torch.from_numpy(A.indptr.astype(np.int64)).cuda()
+        dp.col = torch.from_numpy(A.indices.astype(np.int64)).cuda()
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    out = []
+    for sym, shape in ((1, 9), (0, 0)):
+        o = rmg.default_options(levels=nlev, precision=rmg.FP32, tile_shape=shape)
+        o.smoother, o.nu1, o.nu2, o.cheb_degree = rmg.CHEBYSHEV, 1, 1, 3
+        o.symmetric_storage = sym
+        h = rmg.Hierarchy(lay, o)
+        assert h.tile_shape(0) == ((32, 8, 0) if sym else (0, 0, 0))
+        assert h.coef_planes(0) == (27 if (perturb or not sym) else 14)
+        z = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+        h.vcycle(dp.b, z)
+        out.append((z, h.lam(0)))
+        h.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(_bits(out[0][0]), _bits(out[1][0]))
