@@ -411,150 +411,258 @@ __device__ __forceinline__ bool affine_holds(int c, const int4& a, const RegionD
   return l < R.nz && j < R.ny && i < R.nx;
 }
 
-// One regional node per thread and one row component c per blockIdx.y: the thread scans the
-// CSR row g * B + c once and writes every entry straight into its coefficient stream
-// coef[((c * B + c') * S + slot) * n_r + n] (threads of a warp are consecutive nodes, so for
-// interior rows the stores of one entry index are contiguous). A slot that receives no entry
-// is zeroed at the end; the diagonal slot takes the nullspace rule; a repeated column (not
+// The split of one CSR row: regional node n of region R (local index li), row component c_row.
+// Every entry is handled in the row's order: zsum collects the whole row (A 1 at the node),
+// offsum the regional off-diagonal values written, and the entry goes straight into its
+// coefficient stream coef[((c * B + c') * S + slot) * n_r + n]. At the end a slot that received
+// no entry is zeroed and the diagonal slot takes the nullspace rule; a repeated column (not
 // produced by a well-formed CSR) is accumulated.
-// Resident blocks per SM the split may be compiled for (unset: the compiler's own register
-// choice), and the entries whose loads it batches.
-#ifdef RMG_SPLIT_MIN_BLOCKS
-#define RMG_SPLIT_BOUNDS __launch_bounds__(kTile, RMG_SPLIT_MIN_BLOCKS)
-#else
-#define RMG_SPLIT_BOUNDS __launch_bounds__(kTile)
-#endif
+template <int KIND, int B>
+struct RowSplit {
+  using S = Sten<KIND>;
+  RegionDev R;
+  int n, i, j, l, g, nodes, n_r;
+  bool shared, fast, peel;
+  int4 af;
+  double zsum[B], offsum[B];
+  unsigned seen[B];                            // slots already written (27 < 32 bits)
+  double* cbase;
+
+  __device__ __forceinline__ void begin(int n_, int li, int region, const RegionDev& R_,
+                                        int c_row, int n_r_, const int* __restrict__ gid,
+                                        const uint8_t* __restrict__ mult,
+                                        const int4* __restrict__ affine, double* coef) {
+    R = R_;
+    n = n_;
+    n_r = n_r_;
+    decode(li, R, i, j, l);
+    nodes = R.nx * R.ny * R.nz;
+    peel = R.nx >= 3 && R.ny >= 3;             // box_offset is exact
+    g = gid[n];
+    shared = mult[n] > 1;
+    // rows of single-copy nodes of a region whose gid map is affine (k_affine_*) find the slot
+    // of every entry from c - g alone, without the composite-indexed gathers
+    af = affine[region];
+    fast = af.w != 0 && !shared;
+#pragma unroll
+    for (int b = 0; b < B; ++b) { zsum[b] = 0.0; offsum[b] = 0.0; seen[b] = 0u; }
+    cbase = coef + (size_t)c_row * B * S::S * n_r + n;
+  }
+
+  // Composite node of a column (its component in cp), or -1 for an id out of range (flagged).
+  __device__ __forceinline__ int node_of(int64_t c64, int ncomp, int* err, int& cp) const {
+    cp = 0;
+    if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); return -1; }
+    int c = (int)c64;
+    if (B > 1) {                                 // compile-time divisor: multiply-shift
+      c = (int)(c64 / B);
+      cp = (int)(c64 - (int64_t)c * B);
+    }
+    return c;
+  }
+
+  // Whether entry c needs its interface group (the general path's first gather).
+  __device__ __forceinline__ bool needs_group(int c) const { return c != g && !fast; }
+
+  // One entry, in row order; grp = cgrp[c] when needs_group(c).
+  __device__ __forceinline__ void apply(int c, int b, double v, int grp,
+                                        const int* __restrict__ c2r,
+                                        const int* __restrict__ cgrp,
+                                        const int* __restrict__ gptr,
+                                        const int* __restrict__ gslot,
+                                        const int* __restrict__ rid, int* err) {
+    zsum[b] += v;
+    if (c == g) return;
+    int dx, dy, dz;
+    if (fast) {
+      // c = g + dx + gy dy + gz dz inside the 3x3x3 box: when that position lies in the
+      // region, c is the node there (the map is affine over the region). Any other column is
+      // a node of this region (outside the stencil: the error below, as on the general path)
+      // or of other regions only (skipped, as there).
+      box_offset_affine(c - g, af.y, af.z, dx, dy, dz);
+      const bool in_region = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
+                             j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
+      if (!in_region) {
+        if (affine_holds(c, af, R)) set_err(err, DERR_STENCIL);
+        return;
+      }
+    } else {
+      // regional slot of c inside this region
+      int sc = -1;
+      if (grp < 0) {
+        const int s0 = c2r[c];
+        sc = (s0 >= R.off && s0 < R.off + nodes) ? s0 : -1;
+      } else {
+        for (int q = gptr[grp]; q < gptr[grp + 1]; ++q) {
+          const int s0 = gslot[q];
+          if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
+        }
+      }
+      if (sc < 0) return;                        // entry belongs to other regions only
+      if (peel) {
+        box_offset(sc - n, R.nx, R.nx * R.ny, dx, dy, dz);
+      } else {
+        int ic, jc, lc;
+        decode(sc - R.off, R, ic, jc, lc);
+        dx = ic - i; dy = jc - j; dz = lc - l;
+      }
+    }
+    const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
+                        j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
+    const int slot = inside ? sten_slot<KIND>(dx, dy, dz) : -1;
+    if (slot < 0) { set_err(err, DERR_STENCIL); return; }
+    const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
+    const double vs = q == 1 ? v : v * inv_mult<double>(q);
+    offsum[b] += vs;
+    double* dst = cbase + ((size_t)b * S::S + slot) * n_r;
+    const unsigned bit = 1u << slot;
+    if (seen[b] & bit) {
+      *dst += vs;
+    } else {
+      seen[b] |= bit;
+      *dst = vs;
+    }
+  }
+
+  __device__ __forceinline__ void end(const uint8_t* __restrict__ mult) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      double* cb = cbase + (size_t)b * S::S * n_r;
+#pragma unroll
+      for (int s = 0; s < S::S; ++s)
+        if (s != S::CENTER && !((seen[b] >> s) & 1u)) cb[(size_t)s * n_r] = 0.0;
+      cb[(size_t)S::CENTER * n_r] = zsum[b] * inv_mult<double>(mult[n]) - offsum[b];
+    }
+  }
+};
+
+#define RMG_SPLIT_PARAMS                                                                  \
+  const int* __restrict__ gid, const uint8_t* __restrict__ mult,                          \
+      const int* __restrict__ c2r, const int* __restrict__ cgrp,                          \
+      const int* __restrict__ gptr, const int* __restrict__ gslot,                        \
+      const int* __restrict__ rid, const int4* __restrict__ affine,                       \
+      const int64_t* __restrict__ rowptr, const int64_t* __restrict__ col,                \
+      const double* __restrict__ val, int ncomp, double* __restrict__ coef, int* err
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Entries of a row staged per pass: 27 = 3 x 9 (a shared row stride of 9 words of 8 bytes
+// keeps the lanes' reads of their own rows free of bank conflicts).
+constexpr int kSplitChunk = 9;
+
+// Single-copy rows (the rows of shared nodes are left to k_split_shared, so that a warp of
+// single-copy rows does not wait on the longer path of the interface rows among them). A warp
+// takes 32 consecutive nodes of a tile. Their CSR rows are staged through shared memory nine
+// entries at a time, the lanes copying the 32 rows' entries together (the rows of consecutive
+// nodes lie side by side in the CSR, so each pass reads whole sectors once); then every lane
+// handles its own row's entries in order.
+template <int KIND, int B>
+__global__ void __launch_bounds__(kTile)
+k_split_csr(Grid G, RMG_SPLIT_PARAMS) {
+  constexpr int kWarps = kTile / 32;
+  __shared__ __align__(16) int64_t s_col[kWarps][32 * kSplitChunk];
+  __shared__ __align__(16) double s_val[kWarps][32 * kSplitChunk];
+  __shared__ int64_t s_e0[kWarps][32];           // first entry and length of every lane's row
+  __shared__ int s_len[kWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t* wc = s_col[warp];
+  double* wv = s_val[warp];
+  const int c_row = blockIdx.y;
+  const int tasks = G.ntiles * kWarps;
+  for (int task = blockIdx.x * kWarps + warp; task < tasks; task += gridDim.x * kWarps) {
+    const Tile tile = G.tiles[task / kWarps];
+    const RegionDev R = G.regions[tile.region];
+    const int li = tile.start + (task % kWarps) * 32 + lane;
+    const int n = R.off + li;
+    const bool active = li < R.nx * R.ny * R.nz && mult[n] == 1;
+    RowSplit<KIND, B> rs;
+    int64_t e0 = 0;
+    int len = 0;
+    if (active) {
+      rs.begin(n, li, tile.region, R, c_row, G.n_r, gid, mult, affine, coef);
+      const int64_t row = (int64_t)rs.g * B + c_row;
+      e0 = rowptr[row];
+      len = (int)(rowptr[row + 1] - e0);
+    }
+    s_e0[warp][lane] = e0;
+    s_len[warp][lane] = len;
+    __syncwarp();
+    const int passes = ((int)__reduce_max_sync(0xffffffffu, (unsigned)len) + kSplitChunk - 1) /
+                       kSplitChunk;
+    for (int h = 0; h < passes; ++h) {
+      // entry h * 9 + k of the row of lane r goes to w*[r * 9 + k]
+#pragma unroll 3
+      for (int m = 0; m < kSplitChunk; ++m) {
+        const int idx = lane + 32 * m;
+        const int r = idx / kSplitChunk, k = idx - r * kSplitChunk;
+        const int e = h * kSplitChunk + k;
+        if (e < s_len[warp][r]) {
+          const int64_t at = s_e0[warp][r] + e;
+          cp_async8(wc + idx, col + at);
+          cp_async8(wv + idx, val + at);
+        }
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncwarp();
+      if (active) {
+        const int kn = min(kSplitChunk, len - h * kSplitChunk);
+        for (int k = 0; k < kn; ++k) {
+          int cp;
+          const int c = rs.node_of(wc[lane * kSplitChunk + k], ncomp, err, cp);
+          if (c < 0) continue;
+          const int grp = rs.needs_group(c) ? cgrp[c] : -2;
+          rs.apply(c, cp, wv[lane * kSplitChunk + k], grp, c2r, cgrp, gptr, gslot, rid, err);
+        }
+      }
+      __syncwarp();                              // before the next pass overwrites the rows
+    }
+    if (active) rs.end(mult);
+  }
+}
+
+// Rows of shared nodes, one thread per regional copy, in group-slot order (the copies of one
+// composite node are neighbours, so their common CSR row is read once into L1). The entries
+// go in batches: the column, value and group loads of a batch are issued together (they do not
+// depend on each other), then the entries are applied in order.
 #ifndef RMG_SPLIT_BATCH
 #define RMG_SPLIT_BATCH 4
 #endif
-
 template <int KIND, int B>
-__global__ void RMG_SPLIT_BOUNDS
-k_split_csr(Grid G, const int* __restrict__ gid, const uint8_t* __restrict__ mult,
-            const int* __restrict__ c2r, const int* __restrict__ cgrp,
-            const int* __restrict__ gptr, const int* __restrict__ gslot,
-            const int* __restrict__ rid, const int4* __restrict__ affine,
-            const int64_t* __restrict__ rowptr,
-            const int64_t* __restrict__ col, const double* __restrict__ val, int ncomp,
-            double* __restrict__ coef, int* err) {
-  using S = Sten<KIND>;
+__global__ void __launch_bounds__(kTile)
+k_split_shared(int nslots, const RegionDev* __restrict__ regions, int n_r, RMG_SPLIT_PARAMS) {
   const int c_row = blockIdx.y;
-  RMG_FOR_NODES(G)
-    int i, j, l;
-    decode(li, R, i, j, l);
-    const int nodes = R.nx * R.ny * R.nz;
-    const int sy = R.nx, sz = R.nx * R.ny;
-    const bool peel = R.nx >= 3 && R.ny >= 3;    // box_offset is exact
-    const int g = gid[n];
-    const bool shared = mult[n] > 1;
-    // rows of single-copy nodes of a region whose gid map is affine (k_affine_*) find the slot
-    // of every entry from c - g alone, without the composite-indexed gathers
-    const int4 af = affine[tile_.region];
-    const bool fast = af.w != 0 && !shared;
-    double zsum[B], offsum[B];
-    unsigned seen[B];                            // slots already written (27 < 32 bits)
-#pragma unroll
-    for (int b = 0; b < B; ++b) { zsum[b] = 0.0; offsum[b] = 0.0; seen[b] = 0u; }
-    double* cbase = coef + (size_t)c_row * B * S::S * G.n_r + n;
-    const int64_t row = (int64_t)g * B + c_row;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += gridDim.x * blockDim.x) {
+    const int n = gslot[q];
+    const int r = rid[n];
+    const RegionDev R = regions[r];
+    RowSplit<KIND, B> rs;
+    rs.begin(n, n - R.off, r, R, c_row, n_r, gid, mult, affine, coef);
+    const int64_t row = (int64_t)rs.g * B + c_row;
     const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
-    // entries in batches of four: the column, value and group loads of a batch are issued
-    // together (they do not depend on each other), then the entries are applied in order
     constexpr int U = RMG_SPLIT_BATCH;
     for (int64_t eb = e0; eb < e1; eb += U) {
-      int64_t cc[U];
+      int cn[U], cp[U], grp[U];
       double vv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        cc[u] = eb + u < e1 ? col[eb + u] : -1;
-        vv[u] = eb + u < e1 ? val[eb + u] : 0.0;
-      }
-      int cn[U], cp[U], grp[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        cn[u] = -1;
-        cp[u] = 0;
-        grp[u] = -2;
-        if (eb + u >= e1) continue;
-        const int64_t c64 = cc[u];
-        if (c64 < 0 || c64 >= (int64_t)ncomp * B) { set_err(err, DERR_GID_RANGE); continue; }
-        int c = (int)c64;
-        if (B > 1) {                               // compile-time divisor: multiply-shift
-          c = (int)(c64 / B);
-          cp[u] = (int)(c64 - (int64_t)c * B);
-        }
-        cn[u] = c;
-        if (c != g && !fast) grp[u] = cgrp[c];
+        const bool in = eb + u < e1;
+        const int64_t c64 = in ? col[eb + u] : 0;
+        vv[u] = in ? val[eb + u] : 0.0;
+        cn[u] = in ? rs.node_of(c64, ncomp, err, cp[u]) : -1;
+        if (!in) cp[u] = 0;
+        grp[u] = (cn[u] >= 0 && rs.needs_group(cn[u])) ? cgrp[cn[u]] : -2;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = cn[u];
-        if (c < 0) continue;                       // past the row, or an error
-        const int b = cp[u];
-        const double v = vv[u];
-        zsum[b] += v;
-        if (c == g) continue;
-        int dx, dy, dz;
-        if (fast) {
-          // c = g + dx + gy dy + gz dz inside the 3x3x3 box: when that position lies in the
-          // region, c is the node there (the map is affine over the region). Any other column
-          // is a node of this region (outside the stencil: the error below, as on the general
-          // path) or of other regions only (skipped, as there).
-          box_offset_affine(c - g, af.y, af.z, dx, dy, dz);
-          const bool in_region = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
-                                 j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
-          if (!in_region) {
-            if (affine_holds(c, af, R)) set_err(err, DERR_STENCIL);
-            continue;
-          }
-        } else {
-          // regional slot of c inside this region (its group was loaded above)
-          int sc = -1;
-          if (grp[u] < 0) {
-            const int s0 = c2r[c];
-            sc = (s0 >= R.off && s0 < R.off + nodes) ? s0 : -1;
-          } else {
-            for (int q = gptr[grp[u]]; q < gptr[grp[u] + 1]; ++q) {
-              const int s0 = gslot[q];
-              if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
-            }
-          }
-          if (sc < 0) continue;                    // entry belongs to other regions only
-          if (peel) {
-            box_offset(sc - n, sy, sz, dx, dy, dz);
-          } else {
-            int ic, jc, lc;
-            decode(sc - R.off, R, ic, jc, lc);
-            dx = ic - i; dy = jc - j; dz = lc - l;
-          }
-        }
-        const bool inside = dx >= -1 && dx <= 1 && i + dx >= 0 && i + dx < R.nx &&
-                            j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
-        const int slot = inside ? sten_slot<KIND>(dx, dy, dz) : -1;
-        if (slot < 0) { set_err(err, DERR_STENCIL); continue; }
-        const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
-        const double vs = q == 1 ? v : v * inv_mult<double>(q);
-        offsum[b] += vs;
-        double* dst = cbase + ((size_t)b * S::S + slot) * G.n_r;
-        const unsigned bit = 1u << slot;
-        if (seen[b] & bit) {
-          *dst += vs;
-        } else {
-          seen[b] |= bit;
-          *dst = vs;
-        }
-      }
+      for (int u = 0; u < U; ++u)
+        if (cn[u] >= 0) rs.apply(cn[u], cp[u], vv[u], grp[u], c2r, cgrp, gptr, gslot, rid, err);
     }
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-      double* cb = cbase + (size_t)b * S::S * G.n_r;
-#pragma unroll
-      for (int s = 0; s < S::S; ++s)
-        if (s != S::CENTER && !((seen[b] >> s) & 1u)) cb[(size_t)s * G.n_r] = 0.0;
-      cb[(size_t)S::CENTER * G.n_r] = zsum[b] * inv_mult<double>(mult[n]) - offsum[b];
-    }
-  RMG_END_FOR_NODES
+    rs.end(mult);
+  }
 }
+#undef RMG_SPLIT_PARAMS
 
 // Composite vectors with B dofs per node are node-major (dof g*B + c); regional vectors are
 // component-major (c * n_r + n).
@@ -601,12 +709,24 @@ void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, co
     RMG_LAUNCHED();
   }
   if (L.affine.n < (size_t)L.nreg) build_affine(c, L);
-  const dim3 gb(persistent_grid(c, G.ntiles), B);
+  // single-copy rows over the tiles, then the rows of shared nodes over the group slots; both
+  // grids are one resident wave
+#define RMG_SPLIT_ARGS                                                                     \
+  L.gid.get(), L.mult.get(), L.c2r.get(), L.cgrp.get(), L.gptr.get(), L.gslot.get(),        \
+      L.rid.get(), L.affine.get(), rowptr, col, val, L.ncomp, L.coef.get(), c.d_err.get()
 #define RMG_SPLIT(K, BB)                                                                    \
-  k_split_csr<K, BB><<<gb, kTile, 0, c.stream>>>(G, L.gid.get(), L.mult.get(), L.c2r.get(), \
-                                                 L.cgrp.get(), L.gptr.get(), L.gslot.get(),  \
-                                                 L.rid.get(), L.affine.get(), rowptr, col,   \
-                                                 val, L.ncomp, L.coef.get(), c.d_err.get())
+  do {                                                                                      \
+    const dim3 gb(persistent_grid(c, G.ntiles, resident_per_sm((const void*)k_split_csr<K, BB>)), \
+                  B);                                                                       \
+    k_split_csr<K, BB><<<gb, kTile, 0, c.stream>>>(G, RMG_SPLIT_ARGS);                      \
+    if (L.nslots) {                                                                         \
+      const dim3 gs(persistent_grid(c, (L.nslots + kTile - 1) / kTile,                      \
+                                    resident_per_sm((const void*)k_split_shared<K, BB>)),   \
+                    B);                                                                     \
+      k_split_shared<K, BB><<<gs, kTile, 0, c.stream>>>(L.nslots, L.regions.get(), L.n_r,   \
+                                                        RMG_SPLIT_ARGS);                    \
+    }                                                                                       \
+  } while (0)
   switch (kind) {
     case 5: RMG_SPLIT(5, 1); break;
     case 7: RMG_SPLIT(7, 1); break;
@@ -614,6 +734,7 @@ void split_from_csr(Ctx& c, Level& L, int kind, int B, const int64_t* rowptr, co
     default: if (B == 3) RMG_SPLIT(27, 3); else RMG_SPLIT(27, 1); break;
   }
 #undef RMG_SPLIT
+#undef RMG_SPLIT_ARGS
   RMG_LAUNCHED();
   c.check_device_error("rmg_operator_from_csr");
 }
