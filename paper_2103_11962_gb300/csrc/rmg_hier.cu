@@ -776,7 +776,11 @@ static void galerkin_t(Hier& h, int l, const Level& F, Level& C, const T* fcoef,
   T* cco = ccoef + (size_t)blk * C.kind * C.n_r;
   const double mdiag = (blk / F.B == blk % F.B) ? 1.0 : 0.0;
 #define RMG_RAP(FK, CK, D)                                                                    \
-  if (sizeof(T) == 4) {                                                                       \
+  if (sizeof(T) == 4 && FK == 27 && D == 3) {                                                \
+    const int ga = persistent_grid(c, Gf.ntiles, resident_per_sm((const void*)k_ap_tensor27)); \
+    k_ap_tensor27<<<ga, kTile, 0, c.stream>>>(Gf, C.regions.get(), (const float*)fco,          \
+                                              F.mask.get(), C.mask.get(), (float*)ap);        \
+  } else if (sizeof(T) == 4) {                                                                \
     k_ap_axis32<FK, D><<<gf, kTile, 0, c.stream>>>(Gf, C.regions.get(), (const float*)fco,     \
                                                    F.mask.get(), C.mask.get(), (float*)ap);   \
   } else {                                                                                    \
