@@ -125,6 +125,59 @@ def test_host_csr_split_matches_device_csr(ctx, name):
         lay.operator_from_host_csr(p.stencil, 2, *host)
 
 
+def _renumbered_split(ctx, p, A, seed=3):
+    """Level-0 region stencils of the same operator under the original composite numbering
+    and under a random renumbering (entries kept in their row order)."""
+    from paper_2103_11962_gb300 import rmg
+    A = A.tocsr()
+    out = []
+    for permute in (False, True):
+        perm = (np.random.default_rng(seed).permutation(p.n_nodes) if permute
+                else np.arange(p.n_nodes))
+        inv = np.argsort(perm)
+        counts = np.diff(A.indptr)[inv]
+        rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        take = np.concatenate([np.arange(A.indptr[g], A.indptr[g + 1]) for g in inv])
+        col = perm[A.indices[take]].astype(np.int64)
+        val = A.data[take].astype(np.float64)
+        gids = torch.from_numpy(perm[np.asarray(p.region_gids)].astype(np.int64)).cuda()
+        dirn = np.zeros(p.n_nodes, dtype=np.uint8)
+        dirn[perm] = np.asarray(p.dirichlet, dtype=np.uint8)
+        lay = rmg.Layout(ctx, p.dim, p.region_dims, gids, p.n_nodes,
+                         torch.from_numpy(dirn).cuda())
+        lay.operator_from_csr(p.stencil, torch.from_numpy(rowptr).cuda(),
+                              torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda())
+        h = rmg.Hierarchy(lay, rmg.default_options(levels=2))
+        n_r, _, kind = h.level_sizes(0)
+        coef = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
+        h.level_export(0, coeffs=coef)
+        torch.cuda.synchronize()
+        out.append(coef.cpu().numpy())
+        h.close()
+        lay.close()
+    return out
+
+
+def test_split_skips_couplings_to_other_regions_on_both_paths(ctx):
+    """A symmetric pair of entries between interior nodes of two different regions couples no
+    node of either region's own matrix: both the arithmetic shortcut of affine regions and the
+    general path skip it in the off-diagonals (the diagonal keeps it through A 1), so the two
+    give the same region stencils bit for bit."""
+    import scipy.sparse as sp
+    p, _ = _problem("diff3d_small")
+    A = p.A.tolil(copy=True)
+    gids = np.asarray(p.region_gids)
+    dims = np.asarray(p.region_dims)
+    off = np.concatenate([[0], np.cumsum(np.prod(dims, axis=1))])
+    a = int(gids[off[0] + 2 + dims[0][0] * (2 + dims[0][1] * 2)])      # (2,2,2) of region 0
+    last = len(dims) - 1
+    b = int(gids[off[last] + 3 + dims[last][0] * (3 + dims[last][1] * 3)])
+    A[a, b] = -0.25
+    A[b, a] = -0.25
+    fast, general = _renumbered_split(ctx, p, sp.csr_matrix(A))
+    assert np.array_equal(fast, general)
+
+
 @pytest.mark.parametrize("name", ["diff3d_small", "q1_3d_small", "q1_2d"])
 def test_split_without_affine_numbering(ctx, name):
     """The split takes a shortcut for single-copy rows of regions whose composite ids are
@@ -132,34 +185,9 @@ def test_split_without_affine_numbering(ctx, name):
     (rows and columns of A, gids and Dirichlet flags alike, entries kept in their row order)
     leaves no region affine, so every row takes the general path: the region stencils must be
     the same bit for bit."""
-    from paper_2103_11962_gb300 import rmg, upload
     p, _ = _problem(name)
-    dp = upload(p)
-    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
-    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
-    h = rmg.Hierarchy(lay, rmg.default_options(levels=2))
-    n_r, _, kind = h.level_sizes(0)
-    ref = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
-    h.level_export(0, coeffs=ref)
-    A = p.A.tocsr()
-    perm = np.random.default_rng(3).permutation(p.n_nodes)        # old id -> new id
-    inv = np.argsort(perm)                                         # new id -> old id
-    counts = np.diff(A.indptr)[inv]
-    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    take = np.concatenate([np.arange(A.indptr[g], A.indptr[g + 1]) for g in inv])
-    col = perm[A.indices[take]].astype(np.int64)
-    val = A.data[take].astype(np.float64)
-    gids = torch.from_numpy(perm[np.asarray(p.region_gids)].astype(np.int64)).cuda()
-    dirn = np.zeros(p.n_nodes, dtype=np.uint8)
-    dirn[perm] = np.asarray(p.dirichlet, dtype=np.uint8)
-    lay2 = rmg.Layout(ctx, p.dim, p.region_dims, gids, p.n_nodes, torch.from_numpy(dirn).cuda())
-    lay2.operator_from_csr(p.stencil, torch.from_numpy(rowptr).cuda(),
-                           torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda())
-    h2 = rmg.Hierarchy(lay2, rmg.default_options(levels=2))
-    got = torch.empty_like(ref)
-    h2.level_export(0, coeffs=got)
-    torch.cuda.synchronize()
-    assert torch.equal(got, ref)
+    fast, general = _renumbered_split(ctx, p, p.A)
+    assert np.array_equal(fast, general)
 
 
 @pytest.mark.parametrize("name", list(CASES))
