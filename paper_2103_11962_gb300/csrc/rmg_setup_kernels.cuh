@@ -235,8 +235,10 @@ k_ap_tensor27(Grid Gf, const RegionDev* __restrict__ cregs, const float* __restr
           for (int dx = 0; dx < 3; ++dx) {
             const int gx = x + dx - 1, gy = y + dy - 1, gz = z + dz - 1;
             if (gx < 0 || gx >= R.nx || gy < 0 || gy >= R.ny || gz < 0 || gz >= R.nz) continue;
-            if (fmask[R.off + gx + R.nx * (gy + R.ny * gz)]) continue;
-            const float v = fcoef[(size_t)(dx + 3 * dy + 9 * dz) * Gf.n_r + n];
+            // the coefficient and the neighbour's mask are loaded independently (no round trip
+            // between them); a masked neighbour contributes a zero product
+            const float cv = fcoef[(size_t)(dx + 3 * dy + 9 * dz) * Gf.n_r + n];
+            const float v = fmask[R.off + gx + R.nx * (gy + R.ny * gz)] ? 0.f : cv;
 #pragma unroll
             for (int kx = 0; kx < 3; ++kx) t1[kx] = fmaf(v, wx[dx][kx], t1[kx]);
           }

@@ -162,7 +162,9 @@ def test_split_skips_couplings_to_other_regions_on_both_paths(ctx):
     """A symmetric pair of entries between interior nodes of two different regions couples no
     node of either region's own matrix: both the arithmetic shortcut of affine regions and the
     general path skip it in the off-diagonals (the diagonal keeps it through A 1), so the two
-    give the same region stencils bit for bit."""
+    give the same region stencils bit for bit. The pair is added as the positive semi-definite
+    edge matrix 0.25 [[1, -1], [-1, 1]], so A 1 and the hierarchy's coarse operators stay as
+    they were."""
     import scipy.sparse as sp
     p, _ = _problem("diff3d_small")
     A = p.A.tolil(copy=True)
@@ -174,6 +176,8 @@ def test_split_skips_couplings_to_other_regions_on_both_paths(ctx):
     b = int(gids[off[last] + 3 + dims[last][0] * (3 + dims[last][1] * 3)])
     A[a, b] = -0.25
     A[b, a] = -0.25
+    A[a, a] += 0.25
+    A[b, b] += 0.25
     fast, general = _renumbered_split(ctx, p, sp.csr_matrix(A))
     assert np.array_equal(fast, general)
 
