@@ -422,7 +422,7 @@ struct RowSplit {
   using S = Sten<KIND>;
   RegionDev R;
   int n, i, j, l, g, nodes, n_r;
-  bool shared, fast, peel;
+  bool shared, affine_map, peel;
   int4 af;
   double zsum[B], offsum[B];
   unsigned seen[B];                            // slots already written (27 < 32 bits)
@@ -440,10 +440,11 @@ struct RowSplit {
     peel = R.nx >= 3 && R.ny >= 3;             // box_offset is exact
     g = gid[n];
     shared = mult[n] > 1;
-    // rows of single-copy nodes of a region whose gid map is affine (k_affine_*) find the slot
-    // of every entry from c - g alone, without the composite-indexed gathers
+    // rows of a region whose gid map is affine (k_affine_*) find the slot of every entry from
+    // c - g alone, without the composite-indexed gathers (a shared row still counts the regions
+    // that hold both ends of each coupling, share_count)
     af = affine[region];
-    fast = af.w != 0 && !shared;
+    affine_map = af.w != 0;
 #pragma unroll
     for (int b = 0; b < B; ++b) { zsum[b] = 0.0; offsum[b] = 0.0; seen[b] = 0u; }
     cbase = coef + (size_t)c_row * B * S::S * n_r + n;
@@ -462,7 +463,7 @@ struct RowSplit {
   }
 
   // Whether entry c needs its interface group (the general path's first gather).
-  __device__ __forceinline__ bool needs_group(int c) const { return c != g && !fast; }
+  __device__ __forceinline__ bool needs_group(int c) const { return c != g && !affine_map; }
 
   // One entry, in row order; grp = cgrp[c] when needs_group(c).
   __device__ __forceinline__ void apply(int c, int b, double v, int grp,
@@ -474,7 +475,7 @@ struct RowSplit {
     zsum[b] += v;
     if (c == g) return;
     int dx, dy, dz;
-    if (fast) {
+    if (affine_map) {
       // c = g + dx + gy dy + gz dz inside the 3x3x3 box: when that position lies in the
       // region, c is the node there (the map is affine over the region). Any other column is
       // a node of this region (outside the stencil: the error below, as on the general path)
