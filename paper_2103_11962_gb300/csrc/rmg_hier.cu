@@ -1143,23 +1143,30 @@ static bool coarse_factor_mixed(Hier& h, int nd) {
 static void level0_to_fp32(Hier& h) {
   Ctx& c = *h.c;
   Level& L = *h.lv[0];
-  const size_t nco = (size_t)L.B * L.B * L.kind * L.n_r;
-  const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
-  k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
-  RMG_LAUNCHED();
-  if (!h.half_on) return;
-  // the FP32 cycle's half planes and the flag that says whether they hold the operator
+  if (!h.half_on) {
+    const size_t nco = (size_t)L.B * L.B * L.kind * L.n_r;
+    const int g = persistent_grid(c, (int)std::min<size_t>((nco + 255) / 256, 1 << 20));
+    k_convert<double, float><<<g, 256, 0, c.stream>>>(nco, L.coef.get(), L.coef32.get());
+    RMG_LAUNCHED();
+    return;
+  }
+  // with the FP32 cycle's half planes and the flag that says whether they hold the operator,
+  // in the same pass
   h.half32.ensure((size_t)(L.kind + 1) / 2 * L.n_r);
   int* flag = &h.sc.get()->half_asym;
   RMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
   const Grid G = L.grid();
   const int gb = persistent_grid(c, G.ntiles);
+#define RMG_L0(K)                                                                              \
+  k_level0_fp32<K><<<gb, kTile, 0, c.stream>>>(G, L.coef.get(), L.coef32.get(), h.half32.get(), \
+                                               flag)
   switch (L.kind) {
-    case 5: k_half_pack<5><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
-    case 7: k_half_pack<7><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
-    case 9: k_half_pack<9><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
-    default: k_half_pack<27><<<gb, kTile, 0, c.stream>>>(G, L.coef32.get(), h.half32.get(), flag); break;
+    case 5: RMG_L0(5); break;
+    case 7: RMG_L0(7); break;
+    case 9: RMG_L0(9); break;
+    default: RMG_L0(27); break;
   }
+#undef RMG_L0
   RMG_LAUNCHED();
 }
 

@@ -472,7 +472,11 @@ struct RowSplit {
                                         const int* __restrict__ gptr,
                                         const int* __restrict__ gslot,
                                         const int* __restrict__ rid, int* err) {
-    zsum[b] += v;
+    // the row component b of the entry is a run-time index: select it with an unrolled loop
+    // so that the per-component sums stay in registers
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (k == b) zsum[k] += v;
     if (c == g) return;
     int dx, dy, dz;
     if (affine_map) {
@@ -514,15 +518,17 @@ struct RowSplit {
     if (slot < 0) { set_err(err, DERR_STENCIL); return; }
     const int q = shared ? share_count(g, c, rid, cgrp, gptr, gslot) : 1;
     const double vs = q == 1 ? v : v * inv_mult<double>(q);
-    offsum[b] += vs;
     double* dst = cbase + ((size_t)b * S::S + slot) * n_r;
     const unsigned bit = 1u << slot;
-    if (seen[b] & bit) {
-      *dst += vs;
-    } else {
-      seen[b] |= bit;
-      *dst = vs;
-    }
+    bool again = false;
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (k == b) {
+        offsum[k] += vs;
+        again = (seen[k] & bit) != 0;
+        seen[k] |= bit;
+      }
+    if (again) *dst += vs; else *dst = vs;
   }
 
   __device__ __forceinline__ void end(const uint8_t* __restrict__ mult) {

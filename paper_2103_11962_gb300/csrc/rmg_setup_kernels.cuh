@@ -273,6 +273,46 @@ k_ap_tensor27(Grid Gf, const RegionDev* __restrict__ cregs, const float* __restr
   RMG_END_FOR_NODES
 }
 
+// Level 0 of the FP32 cycle in one pass over the FP64 coefficients: the FP32 copy of every
+// plane (for the FP32 Galerkin chain and the asymmetric fallback), and the half planes with the
+// asymmetry flag exactly as k_half_pack forms them from that copy (the same FP32 roundings, so
+// the same planes and the same flag).
+template <int KIND>
+__global__ void __launch_bounds__(kTile)
+k_level0_fp32(Grid G, const double* __restrict__ coef, float* __restrict__ coef32,
+              float* __restrict__ half, int* __restrict__ asym) {
+  using S = Sten<KIND>;
+  static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
+  constexpr int C = S::CENTER;
+  bool bad = false;
+  RMG_FOR_NODES(G)
+    int i, j, l;
+    RMG_DECODE(i, j, l);
+    const int sy = R.nx, sz = R.nx * R.ny;
+#pragma unroll
+    for (int s = 0; s < S::S; ++s) {
+      const float cv = static_cast<float>(coef[(size_t)s * G.n_r + n]);
+      coef32[(size_t)s * G.n_r + n] = cv;
+      if (s < C) continue;
+      half[(size_t)(s - C) * G.n_r + n] = cv;
+      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
+      bool ok = s > C;
+      if (dx < 0) ok &= (i > 0);
+      if (dx > 0) ok &= (i < R.nx - 1);
+      if (dy < 0) ok &= (j > 0);
+      if (dy > 0) ok &= (j < R.ny - 1);
+      if (dz < 0) ok &= (l > 0);
+      if (dz > 0) ok &= (l < R.nz - 1);
+      if (ok) {
+        const float mv = static_cast<float>(
+            coef[(size_t)(S::S - 1 - s) * G.n_r + n + dx + dy * sy + dz * sz]);
+        bad |= __float_as_uint(cv) != __float_as_uint(mv);
+      }
+    }
+  RMG_END_FOR_NODES
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *asym = 1;
+}
+
 template <int DIM, bool CHECK, bool STORED, typename T>
 __device__ __forceinline__ void rtap_sum(const T* __restrict__ ap, int fn_r,
                                          const RegionDev& F, const float* __restrict__ wr,
