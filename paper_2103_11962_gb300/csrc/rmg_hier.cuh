@@ -85,7 +85,7 @@ struct Hier {
   DBuf<double> x, r, z, p, q, zold, tmp;
   DBuf<float> zold32;                        // previous FP32 cycle output (flexible CG)
   double* pinned = nullptr;                  // host-mapped residual read-back
-  // FP32 cycle, scalar operator: level 0 also as half planes (k_half_pack), read by the sweeps
+  // FP32 cycle, scalar operator: level 0 also as half planes (k_level0_fp32), read by the sweeps
   // while the device flag Scalars::half_asym is 0
   bool half_on = false;
   DBuf<float> half32;

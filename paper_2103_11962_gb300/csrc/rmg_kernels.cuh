@@ -168,41 +168,6 @@ __device__ __forceinline__ float stencil_row_half(const float* __restrict__ half
   return au;
 }
 
-// Half planes of a float stencil; *asym becomes 1 when a mirrored pair inside a region differs
-// in any bit (the sweeps then keep reading the full planes).
-template <int KIND>
-__global__ void __launch_bounds__(kTile)
-k_half_pack(Grid G, const float* __restrict__ coef, float* __restrict__ half,
-            int* __restrict__ asym) {
-  using S = Sten<KIND>;
-  static_assert(mirrored_slots<KIND>(), "half storage needs mirrored stencil slots");
-  constexpr int C = S::CENTER;
-  bool bad = false;
-  RMG_FOR_NODES(G)
-    int i, j, l;
-    RMG_DECODE(i, j, l);
-    const int sy = R.nx, sz = R.nx * R.ny;
-#pragma unroll
-    for (int s = C; s < S::S; ++s) {
-      const float cv = coef[(size_t)s * G.n_r + n];
-      half[(size_t)(s - C) * G.n_r + n] = cv;
-      const int dx = S::dx(s), dy = S::dy(s), dz = S::dz(s);
-      bool ok = s > C;
-      if (dx < 0) ok &= (i > 0);
-      if (dx > 0) ok &= (i < R.nx - 1);
-      if (dy < 0) ok &= (j > 0);
-      if (dy > 0) ok &= (j < R.ny - 1);
-      if (dz < 0) ok &= (l > 0);
-      if (dz > 0) ok &= (l < R.nz - 1);
-      if (ok) {
-        const float mv = coef[(size_t)(S::S - 1 - s) * G.n_r + n + dx + dy * sy + dz * sz];
-        bad |= __float_as_uint(cv) != __float_as_uint(mv);
-      }
-    }
-  RMG_END_FOR_NODES
-  if (__syncthreads_or(bad) && threadIdx.x == 0) *asym = 1;
-}
-
 // Phase A of the FP32 cycle on a level with half planes: the half form when the pack found the
 // operator symmetric (*asym == 0), else the full planes as k_stencil.
 template <bool HALF, int KIND, class Epi>
@@ -219,16 +184,8 @@ __device__ __forceinline__ void stencil_pass(const Grid& G, const float* __restr
   RMG_END_FOR_NODES
 }
 
-// Resident blocks per SM the half-plane sweeps may be compiled for (unset: the compiler's
-// own register choice).
-#ifdef RMG_HALF_MIN_BLOCKS
-#define RMG_HALF_BOUNDS __launch_bounds__(kTile, RMG_HALF_MIN_BLOCKS)
-#else
-#define RMG_HALF_BOUNDS __launch_bounds__(kTile)
-#endif
-
 template <int KIND, class Epi>
-__global__ void RMG_HALF_BOUNDS
+__global__ void __launch_bounds__(kTile)
 k_stencil_half(Grid G, const float* __restrict__ coef, const float* __restrict__ half,
                const int* __restrict__ asym, const float* __restrict__ u,
                const uint8_t* __restrict__ mult, float* __restrict__ y, Epi epi) {

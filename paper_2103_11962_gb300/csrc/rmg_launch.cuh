@@ -75,7 +75,7 @@ void launch_groups(Ctx& c, const Level& L, const AT* y, Epi epi, cudaStream_t st
 }
 
 // Phase A over `sweep` (a tuned tile list of L; the level's run tiles when null), then phase B.
-// An FP32 sweep given half planes (see k_half_pack) and their asymmetry flag reads the half
+// An FP32 sweep given half planes (see k_level0_fp32) and their asymmetry flag reads the half
 // form while the flag is 0.
 template <class Epi, typename CT, typename VT, typename AT>
 void launch_stencil(Ctx& c, const Level& L, const CT* coef, const VT* u, AT* y, Epi epi,

@@ -274,9 +274,10 @@ k_ap_tensor27(Grid Gf, const RegionDev* __restrict__ cregs, const float* __restr
 }
 
 // Level 0 of the FP32 cycle in one pass over the FP64 coefficients: the FP32 copy of every
-// plane (for the FP32 Galerkin chain and the asymmetric fallback), and the half planes with the
-// asymmetry flag exactly as k_half_pack forms them from that copy (the same FP32 roundings, so
-// the same planes and the same flag).
+// plane (for the FP32 Galerkin chain and the asymmetric fallback) and the half planes of
+// stencil_row_half (planes C..S-1). *asym becomes 1 when a mirrored pair of the FP32 copy
+// inside a region differs in any bit (the sweeps then keep reading the full planes); the pair's
+// far value is rounded here from its FP64 value, the same rounding that made the copy.
 template <int KIND>
 __global__ void __launch_bounds__(kTile)
 k_level0_fp32(Grid G, const double* __restrict__ coef, float* __restrict__ coef32,
