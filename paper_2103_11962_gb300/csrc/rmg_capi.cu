@@ -1,5 +1,6 @@
 // extern "C" entry points: argument checks, exception -> status translation.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -30,6 +31,48 @@ rmg_status guarded(rmg_ctx* ctx, F&& f) {
   } catch (const std::exception& e) {
     return fail(ctx, RMG_ERR_CUDA, e.what());
   }
+}
+
+// Copy of `bytes` bytes (a multiple of 8, both ends 8-byte aligned) from page-locked host memory
+// that the device can address (src: its device pointer) into device memory, read by the SMs
+// over the host link: 16-byte loads when both ends allow them, else 8-byte ones.
+__global__ void k_copy_from_host(const void* __restrict__ src, void* __restrict__ dst,
+                                 size_t bytes) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+    const int4* s = static_cast<const int4*>(src);
+    int4* d = static_cast<int4*>(dst);
+    const size_t n16 = bytes / 16;
+    for (size_t k = t0; k < n16; k += stride) d[k] = s[k];
+    if (t0 == 0 && (bytes & 15))
+      reinterpret_cast<int64_t*>(dst)[bytes / 8 - 1] =
+          reinterpret_cast<const int64_t*>(src)[bytes / 8 - 1];
+  } else {
+    const int64_t* s = static_cast<const int64_t*>(src);
+    int64_t* d = static_cast<int64_t*>(dst);
+    for (size_t k = t0; k < bytes / 8; k += stride) d[k] = s[k];
+  }
+}
+
+// Host-to-device copy of an array of 8-byte elements on stream st. Page-locked host memory
+// that the driver reports as mapped into the device's address space (cudaPointerGetAttributes:
+// a host allocation with a device pointer) is read by a kernel, which draws more of the host
+// link's bandwidth than a copy-engine transfer; any other host memory goes by cudaMemcpyAsync.
+void copy_host_array(void* dst, const void* src, size_t bytes, cudaStream_t st, int nsm) {
+  if (!bytes) return;
+  cudaPointerAttributes a{};
+  const bool mapped = cudaPointerGetAttributes(&a, src) == cudaSuccess &&
+                      a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
+  if (!mapped || (((uintptr_t)src | (uintptr_t)dst) & 7)) {
+    cudaGetLastError();                          // unregistered memory: not an error
+    RMG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return;
+  }
+  const size_t blocks = std::min<size_t>((bytes / 16 + 255) / 256, (size_t)nsm * 8);
+  k_copy_from_host<<<(unsigned)std::max<size_t>(blocks, 1), 256, 0, st>>>(a.devicePointer, dst,
+                                                                          bytes);
+  RMG_LAUNCHED();
 }
 
 }  // namespace
@@ -158,14 +201,10 @@ rmg_status rmg_operator_from_host_csr(rmg_layout* lay, int stencil, int dofs_per
     lay->csr_rowptr.ensure(nrows + 1);
     lay->csr_col.ensure(std::max<size_t>(nnz, 1));
     lay->csr_val.ensure(std::max<size_t>(nnz, 1));
-    RMG_CUDA(cudaMemcpyAsync(lay->csr_rowptr.get(), rowptr, (nrows + 1) * sizeof(int64_t),
-                             cudaMemcpyHostToDevice, st));
-    if (nnz) {
-      RMG_CUDA(cudaMemcpyAsync(lay->csr_col.get(), col, nnz * sizeof(int64_t),
-                               cudaMemcpyHostToDevice, st));
-      RMG_CUDA(cudaMemcpyAsync(lay->csr_val.get(), val, nnz * sizeof(double),
-                               cudaMemcpyHostToDevice, st));
-    }
+    const int nsm = lay->ctx->c.nsm;
+    copy_host_array(lay->csr_rowptr.get(), rowptr, (nrows + 1) * sizeof(int64_t), st, nsm);
+    copy_host_array(lay->csr_col.get(), col, nnz * sizeof(int64_t), st, nsm);
+    copy_host_array(lay->csr_val.get(), val, nnz * sizeof(double), st, nsm);
     split_from_csr(lay->ctx->c, lay->L0, stencil, dofs_per_node, lay->csr_rowptr.get(),
                    lay->csr_col.get(), lay->csr_val.get());
     lay->ybuf.ensure((size_t)dofs_per_node * lay->L0.n_r);
