@@ -18,7 +18,7 @@ learned and linear weights); this module only moves arrays between those calls.
   stationary solver from the same random error; region k keeps the learned weights when its
   energy reduction (e_k^T A^(k) e_k after / before) is no worse than with linear interpolation.
   Nodes shared with a rejecting region keep linear weights (rmg_hier_blend_weights), so copies
-  stay identical. The plain prolongator is the fallback and the judge: if the blended weights
+  stay identical. The plain prolongator is the fallback and the yardstick: if the blended weights
   give a worse global factor than linear interpolation, linear interpolation is restored.
 """
 from __future__ import annotations
