@@ -412,11 +412,13 @@ __device__ __forceinline__ bool affine_holds(int c, const int4& a, const RegionD
 }
 
 // The split of one CSR row: regional node n of region R (local index li), row component c_row.
-// Every entry is handled in the row's order: zsum collects the whole row (A 1 at the node),
-// offsum the regional off-diagonal values written, and the entry goes straight into its
-// coefficient stream coef[((c * B + c') * S + slot) * n_r + n]. At the end a slot that received
-// no entry is zeroed and the diagonal slot takes the nullspace rule; a repeated column (not
-// produced by a well-formed CSR) is accumulated.
+// Every entry is handled in the row's order and goes straight into its coefficient stream
+// coef[((c * B + c') * S + slot) * n_r + n]. For the diagonal slot's nullspace rule a shared
+// row collects the whole row (zsum = A 1 at the node) and the split off-diagonal values
+// (offsum); a single-copy row, where the two sums would cancel in every in-region coupling,
+// collects only its diagonal entry and its couplings to other regions. At the end a slot that
+// received no entry is zeroed; a repeated column (not produced by a well-formed CSR) is
+// accumulated.
 template <int KIND, int B>
 struct RowSplit {
   using S = Sten<KIND>;
@@ -473,10 +475,12 @@ struct RowSplit {
                                         const int* __restrict__ gslot,
                                         const int* __restrict__ rid, int* err) {
     // the row component b of the entry is a run-time index: select it with an unrolled loop
-    // so that the per-component sums stay in registers
+    // so that the per-component sums stay in registers. A shared row sums every entry (A 1);
+    // a single-copy row only the entries that do not land off the diagonal of its region
+    // (see end())
 #pragma unroll
     for (int k = 0; k < B; ++k)
-      if (k == b) zsum[k] += v;
+      if (k == b && (shared || c == g)) zsum[k] += v;
     if (c == g) return;
     int dx, dy, dz;
     if (affine_map) {
@@ -489,6 +493,7 @@ struct RowSplit {
                              j + dy >= 0 && j + dy < R.ny && l + dz >= 0 && l + dz < R.nz;
       if (!in_region) {
         if (affine_holds(c, af, R)) set_err(err, DERR_STENCIL);
+        else add_outside(b, v);
         return;
       }
     } else {
@@ -503,7 +508,10 @@ struct RowSplit {
           if (s0 >= R.off && s0 < R.off + nodes) { sc = s0; break; }
         }
       }
-      if (sc < 0) return;                        // entry belongs to other regions only
+      if (sc < 0) {                              // entry belongs to other regions only
+        add_outside(b, v);
+        return;
+      }
       if (peel) {
         box_offset(sc - n, R.nx, R.nx * R.ny, dx, dy, dz);
       } else {
@@ -524,11 +532,19 @@ struct RowSplit {
 #pragma unroll
     for (int k = 0; k < B; ++k)
       if (k == b) {
-        offsum[k] += vs;
+        if (shared) offsum[k] += vs;
         again = (seen[k] & bit) != 0;
         seen[k] |= bit;
       }
     if (again) *dst += vs; else *dst = vs;
+  }
+
+  // An entry of a single-copy row that couples to other regions only keeps its place in the
+  // row sum of the nullspace rule.
+  __device__ __forceinline__ void add_outside(int b, double v) {
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (k == b && !shared) zsum[k] += v;
   }
 
   __device__ __forceinline__ void end(const uint8_t* __restrict__ mult) {
@@ -538,7 +554,11 @@ struct RowSplit {
 #pragma unroll
       for (int s = 0; s < S::S; ++s)
         if (s != S::CENTER && !((seen[b] >> s) & 1u)) cb[(size_t)s * n_r] = 0.0;
-      cb[(size_t)S::CENTER * n_r] = zsum[b] * inv_mult<double>(mult[n]) - offsum[b];
+      // the nullspace rule z_i / mult_i - (split off-diagonal sum); with a single copy every
+      // off-diagonal entry in the region enters both terms whole, so the rule is the diagonal
+      // entry plus the entries coupling to other regions, formed without that cancellation
+      cb[(size_t)S::CENTER * n_r] =
+          shared ? zsum[b] * inv_mult<double>(mult[n]) - offsum[b] : zsum[b];
     }
   }
 };
