@@ -99,8 +99,9 @@ def test_layout_and_split(ctx, name):
 
 @pytest.mark.parametrize("name", ["diff3d_small", "q1_2d"])
 def test_host_csr_split_matches_device_csr(ctx, name):
-    """rmg_operator_from_host_csr (host arrays, pageable and page-locked) gives the same
-    region stencils, bit for bit, as the split of the same CSR from device memory."""
+    """rmg_operator_from_host_csr (host arrays: pageable, page-locked, and page-locked at an odd
+    8-byte offset) gives the same region stencils, bit for bit, as the split of the same CSR
+    from device memory."""
     from paper_2103_11962_gb300 import rmg, upload
     p, _ = _problem(name)
     dp = upload(p)
@@ -115,7 +116,15 @@ def test_host_csr_split_matches_device_csr(ctx, name):
             np.ascontiguousarray(A.indices.astype(np.int64)),
             np.ascontiguousarray(A.data.astype(np.float64))]
     pinned = [torch.from_numpy(a).pin_memory() for a in host]
-    for arrays in (host, pinned):
+    # page-locked arrays that start 8 bytes past a 16-byte boundary (the copy kernel's 8-byte
+    # path)
+    shifted = []
+    for a in host:
+        t = torch.empty(a.size + 1, dtype=torch.from_numpy(a).dtype, pin_memory=True)
+        t[1:].copy_(torch.from_numpy(a))
+        shifted.append(t[1:])
+    assert all(t.data_ptr() % 16 == 8 for t in shifted)
+    for arrays in (host, pinned, shifted):
         lay.operator_from_host_csr(p.stencil, 1, *arrays)
         got = torch.empty_like(ref)
         h.level_export(0, coeffs=got)
