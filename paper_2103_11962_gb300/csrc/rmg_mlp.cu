@@ -272,6 +272,95 @@ k_mlp(const float* __restrict__ params, int n, long long ntiles, const float* __
   }  // tiles
 }
 
+// Inference alone: the forward pass of k_mlp (same BF16 roundings, same MMA sequence, same
+// epilogues, so the same outputs) with each warp working through its own tiles of 16 samples.
+// Without the backward buffers a block needs 44 KB of shared memory instead of k_mlp's, so
+// more blocks share an SM, and no block-wide barrier stands between a warp's tiles.
+constexpr int kWarpRows = 16;
+struct MlpInferSmem {
+  __nv_bfloat16 W1b[NH * SX];
+  __nv_bfloat16 W2b[NH * SH];
+  __nv_bfloat16 W3b[8 * SH];
+  __nv_bfloat16 Xb[kThreads / 32][kWarpRows * SX];
+  __nv_bfloat16 Hb[kThreads / 32][kWarpRows * SH];  // layer-1 output, then layer 2's in place
+};
+
+__global__ void __launch_bounds__(kThreads)
+k_mlp_infer(const float* __restrict__ params, int n, const float* __restrict__ feats,
+            float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpInferSmem& S = *reinterpret_cast<MlpInferSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  for (int e = tid; e < NH * NF; e += kThreads)
+    S.W1b[(e / NF) * SX + e % NF] = __float2bfloat16_rn(params[O_W1 + e]);
+  for (int e = tid; e < NH * NH; e += kThreads)
+    S.W2b[(e / NH) * SH + e % NH] = __float2bfloat16_rn(params[O_W2 + e]);
+  for (int e = tid; e < 8 * NH; e += kThreads) {
+    const int j = e / NH, k = e % NH;
+    S.W3b[j * SH + k] = __float2bfloat16_rn(j < NOUT ? params[O_W3 + j * NH + k] : 0.f);
+  }
+  __syncthreads();
+  __nv_bfloat16* X = S.Xb[warp];
+  __nv_bfloat16* H = S.Hb[warp];
+  const long long tiles = ((long long)n + kWarpRows - 1) / kWarpRows;
+  for (long long tile = (long long)blockIdx.x * (kThreads / 32) + warp; tile < tiles;
+       tile += (long long)gridDim.x * (kThreads / 32)) {
+    const long long base = tile * kWarpRows;
+    __syncwarp();                                  // the previous tile's reads are done
+    for (int e = lane; e < kWarpRows * NF; e += 32) {
+      const int r = e / NF, k = e % NF;
+      const long long i = base + r;
+      X[r * SX + k] = __float2bfloat16_rn(i < n ? feats[i * NF + k] : 0.f);
+    }
+    __syncwarp();
+    {
+      float acc[8][4] = {};
+      warp_mma<8, NF>(X, SX, 0, S.W1b, SX, acc);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = params[O_B1 + c], b1 = params[O_B1 + c + 1];
+        H[g * SH + c] = __float2bfloat16_rn(fmaxf(acc[nt][0] + b0, 0.f));
+        H[g * SH + c + 1] = __float2bfloat16_rn(fmaxf(acc[nt][1] + b1, 0.f));
+        H[(g + 8) * SH + c] = __float2bfloat16_rn(fmaxf(acc[nt][2] + b0, 0.f));
+        H[(g + 8) * SH + c + 1] = __float2bfloat16_rn(fmaxf(acc[nt][3] + b1, 0.f));
+      }
+    }
+    __syncwarp();
+    {
+      float acc[8][4] = {};
+      warp_mma<8, NH>(H, SH, 0, S.W2b, SH, acc);
+      __syncwarp();                                // layer 1's values are all read
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = params[O_B2 + c], b1 = params[O_B2 + c + 1];
+        H[g * SH + c] = __float2bfloat16_rn(fmaxf(acc[nt][0] + b0, 0.f));
+        H[g * SH + c + 1] = __float2bfloat16_rn(fmaxf(acc[nt][1] + b1, 0.f));
+        H[(g + 8) * SH + c] = __float2bfloat16_rn(fmaxf(acc[nt][2] + b0, 0.f));
+        H[(g + 8) * SH + c + 1] = __float2bfloat16_rn(fmaxf(acc[nt][3] + b1, 0.f));
+      }
+    }
+    __syncwarp();
+    {
+      float acc[1][4] = {};
+      warp_mma<1, NH>(H, SH, 0, S.W3b, SH, acc);
+      const int c = 2 * t;
+      const float zz[4] = {acc[0][0], acc[0][1], acc[0][2], acc[0][3]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = g + (q >= 2 ? 8 : 0), col = c + (q & 1);
+        const long long i = base + row;
+        if (col < NOUT && i < n) {
+          const float z = zz[q] + params[O_B3 + col];
+          out[i * NOUT + col] = 1.f / (1.f + __expf(-z));
+        }
+      }
+    }
+  }
+}
+
 __global__ void k_adam(int np, float* __restrict__ p, const float* __restrict__ gr,
                        float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
@@ -372,6 +461,24 @@ void mlp_launch(rmg_mlp* net, int n, const float* feats, const float* labels, co
                 int mode, int sample, int rows, unsigned long long seed, float inv_norm,
                 float* out, float* loss) {
   Ctx& c = net->ctx->c;
+  if (mode == 0 && !sample) {                    // inference over samples 0 .. n-1
+    const int smem = (int)sizeof(MlpInferSmem);
+    RMG_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_infer, kThreads, smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    const long long warps = ((long long)n + kWarpRows - 1) / kWarpRows;
+    const long long want = (warps + kThreads / 32 - 1) / (kThreads / 32);
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>(want, (long long)c.nsm * std::max(1, per_sm)));
+    k_mlp_infer<<<blocks, kThreads, smem, c.stream>>>(net->p.get(), n, feats, out);
+    RMG_LAUNCHED();
+    return;
+  }
   const int smem = (int)mlp_smem();
   RMG_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long tiles = (rows + kRows - 1) / kRows;
