@@ -388,6 +388,7 @@ k_features(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ 
     float* f = feats + (size_t)n * NF;
     const double dn = comp_coupling<KIND>(coef, G.n_r, n, St::CENTER, mult, gid, cgrp, gptr, gslot);
     const double dref = dn > 0.0 ? dn : 1.0;
+    const double inv_ref = 1.0 / dref;            // one FP64 division per node, not 21
     const int len[3] = {R.nx, R.ny, R.nz};
     for (int a = 0; a < 3; ++a) {
       int rem = a < St::DIM ? x[a] % 3 : 0;
@@ -402,13 +403,13 @@ k_features(Grid G, const double* __restrict__ coef, const uint8_t* __restrict__ 
       for (int e = 0; e < 3; ++e) {
         const double k = -comp_coupling<KIND>(coef, G.n_r, p0 + e * stride[a], slot, mult, gid,
                                               cgrp, gptr, gslot);
-        const float v = log10f(fmaxf((float)(k / dref), 1e-12f));
+        const float v = log10f(fmaxf((float)(k * inv_ref), 1e-12f));
         f[9 * a + e] = fminf(v, 2.f);
       }
       for (int i = 0; i < 4; ++i) {
         const double d = comp_coupling<KIND>(coef, G.n_r, p0 + i * stride[a], St::CENTER, mult,
                                              gid, cgrp, gptr, gslot);
-        const float v = log10f(fmaxf((float)(d / dref), 1e-12f));
+        const float v = log10f(fmaxf((float)(d * inv_ref), 1e-12f));
         f[9 * a + 3 + i] = fminf(v, 12.f);
       }
       f[9 * a + 7] = (float)(rem / 3.0);
