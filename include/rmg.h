@@ -189,8 +189,8 @@ rmg_status rmg_operator_from_block_csr(rmg_layout* layout, int stencil, int dofs
  * on the context's stream: page-locked host arrays that the driver maps into the device's
  * address space (cudaPointerGetAttributes reports a device pointer) and that are 8-byte
  * aligned are read by a copy kernel over the host link; any other host memory is copied with
- * cudaMemcpyAsync. The host arrays may be reused once the call returns. Errors: RMG_ERR_ARG for null
- * pointers, dofs_per_node other than 1 or 3, or a rowptr that does not start at 0; otherwise
+ * cudaMemcpyAsync. The host arrays may be reused once the call returns. Errors: RMG_ERR_ARG for
+ * null pointers, dofs_per_node other than 1 or 3, or a rowptr that does not start at 0; otherwise
  * those of the device-CSR calls. Synchronises the stream. */
 rmg_status rmg_operator_from_host_csr(rmg_layout* layout, int stencil, int dofs_per_node,
                                       const int64_t* rowptr, const int64_t* col,
