@@ -192,6 +192,37 @@ def test_split_skips_couplings_to_other_regions_on_both_paths(ctx):
 
 
 @pytest.mark.parametrize("name", ["diff3d_small", "q1_3d_small", "q1_2d"])
+def test_split_diagonal_of_single_copy_rows_is_the_matrix_diagonal(ctx, name):
+    """For a node with one copy every in-region coupling enters both sums of the nullspace rule
+    whole, so its split diagonal is A_ii plus its couplings to other regions (none in these
+    box layouts): the split must return A_ii bit for bit, and every off-diagonal of such a row
+    the matrix entry itself."""
+    from paper_2103_11962_gb300 import rmg, upload
+    p, _ = _problem(name)
+    dp = upload(p)
+    lay = rmg.Layout(ctx, p.dim, p.region_dims, dp.gids, p.n_nodes, dp.dirichlet)
+    lay.operator_from_csr(p.stencil, dp.rowptr, dp.col, dp.val)
+    h = rmg.Hierarchy(lay, rmg.default_options(levels=2))
+    n_r, _, kind = h.level_sizes(0)
+    coef = torch.empty(kind * n_r, dtype=torch.float64, device="cuda")
+    h.level_export(0, coeffs=coef)
+    C = coef.cpu().numpy().reshape(kind, n_r)
+    gids = np.asarray(p.region_gids)
+    single = np.bincount(gids, minlength=p.n_nodes)[gids] == 1
+    A = p.A.tocsr()
+    diag = A.diagonal()
+    center = (kind - 1) // 2
+    assert np.array_equal(C[center][single], diag[gids[single]])
+    # off-diagonals of single-copy rows: the stencil entries are the matrix entries themselves
+    M = stencils_to_matrix(p.region_dims, coef.cpu().numpy(), kind).tocoo()
+    keep = single[M.row] & (M.row != M.col)
+    r, c, v = M.row[keep], M.col[keep], M.data[keep]
+    assert np.array_equal(v, np.asarray(A[gids[r], gids[c]]).ravel())
+    h.close()
+    lay.close()
+
+
+@pytest.mark.parametrize("name", ["diff3d_small", "q1_3d_small", "q1_2d"])
 def test_split_without_affine_numbering(ctx, name):
     """The split takes a shortcut for single-copy rows of regions whose composite ids are
     numbered lexicographically (an affine gid map). Renumbering the composite nodes at random
