@@ -174,6 +174,32 @@ def test_split_entries_follow_rule(p3d):
 
 
 @pytest.mark.parametrize("name", ["p2d", "p3d", "q3d"])
+def test_single_copy_rows_split_to_the_matrix_row(name, request):
+    """A node held by one region only has every coupling inside that region with q_ij = 1, so
+    the nullspace rule returns its matrix row unchanged: diagonal A_ii (to rounding of the two
+    sums the oracle forms), off-diagonals A_ij exactly."""
+    p = request.getfixturevalue(name)
+    lay = make_layout(p.region_dims, p.region_gids, p.n_nodes, p.dirichlet)
+    blocks = split_blocks(lay, p.A)
+    A = p.A.tocsr()
+    mult = np.bincount(p.region_gids, minlength=p.n_nodes)
+    for k in range(lay.m):
+        gk = np.asarray(p.region_gids[lay.offsets[k]:lay.offsets[k + 1]])
+        B = blocks[k].tocsr()
+        for li in np.flatnonzero(mult[gk] == 1)[::7]:
+            gi = int(gk[li])
+            row = B.getrow(li)
+            scale = abs(A.getrow(gi).data).max()
+            for lj, v in zip(row.indices, row.data):
+                if lj == li:
+                    assert abs(v - A[gi, gi]) <= 1e-14 * scale
+                else:
+                    assert v == A[gi, int(gk[lj])]
+            # and nothing of the row is lost: same number of couplings
+            assert row.nnz == A.getrow(gi).nnz
+
+
+@pytest.mark.parametrize("name", ["p2d", "p3d", "q3d"])
 def test_single_region_split_equals_whole_problem_split(name, request):
     """The per-region split (used where the whole-problem form is too large) gives exactly the
     blocks of the whole-problem split, which Lemma 1 pins."""
